@@ -1,0 +1,230 @@
+"""Global sparse assembly of the P1-P1 PSPG-stabilised Stokes system on a Kuhn mesh.
+
+Degrees of freedom are numbered component-major ("SoA"): index c*nn + node for component
+c in (u_x, u_y, u_z, p), nn = (n+1)^3 nodes, node index x-fastest.
+
+Paper passages followed here:
+
+* a_sym(u,v) = (2 mu sym grad u, sym grad v)               Sec. 1, eq. (standard)
+* a_tr(u,v)  = a_sym(u,v) - (mu div u, div v)                Sec. 2, eq. (newbil)
+* a_dev(u,v) = (2 mu dev sym grad u, dev sym grad v)         Sec. 2, below eq. (newbil)
+* gradient form (mu grad u, grad v)                         Sec. 4.1 / 4.2.3 (inconsistent)
+* b(v,q) = -(div v, q)                                       Sec. 1, below eq. (weakma)
+* saddle matrix [[A, B^T], [B, -C]]                          Sec. 5, first display
+* C: PSPG / Brezzi-Pitkaranta pressure stabilisation. The paper states only that the
+  equal-order P1-P1 scheme is stabilised (Sec. 4 intro, Sec. 5); we read it as
+  C = sum_T tau_T (grad p, grad q)_T with tau_T = beta h^2 / mu_T (beta = 1/12, h the cube
+  edge), the 1/mu scaling mirroring the 1/(2 mu_i) weight of eq. (stabc).  Its consistent
+  right-hand side is g_q = -sum_T tau_T (f, grad q)_T.
+* boundary conditions: Dirichlet (all components), free-slip (normal component), traction
+  (natural) - Sec. 1, eq. (boundary)
+* interface rows: test functions that are not in H^1_0 of one isoviscous subdomain, i.e. nodes
+  on Gamma_12 or on a traction face - Sec. 2.2, eq. (equivalence-stencil)
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from .mesh import kuhn_tets, node_xyz, p1_geometry
+
+FORMS = ("tr", "sym", "grad", "dev")
+DIRICHLET, FREESLIP, TRACTION = 0, 1, 2
+PSPG_BETA = 1.0 / 12.0
+
+
+def _sym_basis(grad):
+    """sym grad of the vector basis function lambda_a e_i: E[T, a, i] is a 3x3 tensor.
+
+    grad(lambda_a e_i) has entries (e_i)_k (d_l lambda_a) at (k, l)."""
+    nT = grad.shape[0]
+    G = np.zeros((nT, 4, 3, 3, 3))  # [T, a, i, k, l]
+    for i in range(3):
+        G[:, :, i, i, :] = grad
+    return 0.5 * (G + np.swapaxes(G, 3, 4)), G
+
+
+class Discretisation:
+    """All matrices of one grid level (unconstrained), plus constraint and interface sets.
+
+    n      : cells per side; h = 1/n
+    cell_mu: float64 [n^3] viscosity per hexahedral cell (flat index i + n*(j + n*k))
+    face   : six face types (-x, +x, -y, +y, -z, +z)
+    beta   : PSPG constant
+    """
+
+    def __init__(self, n: int, cell_mu: np.ndarray, face, beta: float = PSPG_BETA):
+        self.n = n
+        self.nn = (n + 1) ** 3
+        self.h = 1.0 / n
+        self.cell_mu = np.asarray(cell_mu, dtype=np.float64).ravel()
+        assert self.cell_mu.size == n ** 3 and np.all(self.cell_mu > 0)
+        self.face = tuple(int(f) for f in face)
+        self.beta = beta
+        self.xyz = node_xyz(n)
+        self.tets, self.tet_cell = kuhn_tets(n)
+        self.grad, self.vol = p1_geometry(self.xyz, self.tets)
+        self.mu_T = self.cell_mu[self.tet_cell]
+        self.tau_T = beta * self.h ** 2 / self.mu_T
+        self._cache = {}
+
+    # ------------------------------------------------------------------ element matrices
+    def _assemble(self, vals, rows, cols, shape):
+        return sp.coo_matrix((vals.ravel(), (rows.ravel(), cols.ravel())), shape=shape).tocsr()
+
+    def velocity_block(self, form: str) -> sp.csr_matrix:
+        """A for the chosen bilinear form, unconstrained, [3nn, 3nn], rows = test (b, j).
+
+        Entries are integrals of products of constant element gradients, i.e. |T| times the
+        integrand, written straight from the tensor definitions of the forms."""
+        assert form in FORMS
+        if form in self._cache:
+            return self._cache[form]
+        nn = self.nn
+        E, G = _sym_basis(self.grad)
+        w = self.mu_T * self.vol
+        if form == "sym":
+            # (2 mu sym grad u, sym grad v): u = lambda_a e_i (column), v = lambda_b e_j (row)
+            ent = 2.0 * np.einsum("t,taikl,tbjkl->tbjai", w, E, E)
+        elif form == "tr":
+            div = self.grad  # div(lambda_a e_i) = d_i lambda_a
+            ent = 2.0 * np.einsum("t,taikl,tbjkl->tbjai", w, E, E) - np.einsum(
+                "t,tai,tbj->tbjai", w, div, div)
+        elif form == "grad":
+            ent = np.einsum("t,taikl,tbjkl->tbjai", w, G, G)
+        else:  # dev
+            D = E.copy()
+            tr = np.einsum("taikk->tai", E) / 3.0
+            for k in range(3):
+                D[:, :, :, k, k] -= tr
+            ent = 2.0 * np.einsum("t,taikl,tbjkl->tbjai", w, D, D)
+        nT = self.tets.shape[0]
+        node = self.tets
+        comp = np.arange(3)
+        rows = comp[None, None, :, None, None] * nn + node[:, :, None, None, None]
+        cols = comp[None, None, None, None, :] * nn + node[:, None, None, :, None]
+        rows = np.broadcast_to(rows, (nT, 4, 3, 4, 3))
+        cols = np.broadcast_to(cols, (nT, 4, 3, 4, 3))
+        A = self._assemble(ent, rows, cols, (3 * nn, 3 * nn))
+        self._cache[form] = A
+        return A
+
+    def divergence(self) -> sp.csr_matrix:
+        """B [nn, 3nn]: B[b, (a,i)] = b(lambda_a e_i, lambda_b) = -sum_T d_i lambda_a |T|/4."""
+        nn = self.nn
+        nT = self.tets.shape[0]
+        ent = -np.einsum("t,tai->tai", self.vol / 4.0, self.grad)  # independent of b
+        ent = np.broadcast_to(ent[:, None, :, :], (nT, 4, 4, 3))  # [T, b, a, i]
+        rows = np.broadcast_to(self.tets[:, :, None, None], (nT, 4, 4, 3))
+        cols = np.arange(3)[None, None, None, :] * nn + self.tets[:, None, :, None]
+        cols = np.broadcast_to(cols, (nT, 4, 4, 3))
+        return self._assemble(ent, rows, cols, (nn, 3 * nn))
+
+    def stabilisation(self) -> sp.csr_matrix:
+        """C [nn, nn] = sum_T tau_T |T| grad lambda_a . grad lambda_b."""
+        ent = np.einsum("t,tad,tbd->tba", self.tau_T * self.vol, self.grad, self.grad)
+        nT = self.tets.shape[0]
+        rows = np.broadcast_to(self.tets[:, :, None], (nT, 4, 4))
+        cols = np.broadcast_to(self.tets[:, None, :], (nT, 4, 4))
+        return self._assemble(ent, rows, cols, (self.nn, self.nn))
+
+    def lumped_mass(self) -> np.ndarray:
+        """Row sums of the P1 mass matrix: m_b = sum_{T ni b} |T| / 4."""
+        m = np.zeros(self.nn)
+        np.add.at(m, self.tets.ravel(), np.repeat(self.vol / 4.0, 4))
+        return m
+
+    def pressure_weights(self) -> np.ndarray:
+        """w_b = int lambda_b / mu = sum_{T ni b} |T| / (4 mu_T): the discrete form of the
+        constraint int mu^{-1} q = 0 that fixes the pressure constant (Sec. 1, space Q)."""
+        w = np.zeros(self.nn)
+        np.add.at(w, self.tets.ravel(), np.repeat(self.vol / (4.0 * self.mu_T), 4))
+        return w
+
+    def saddle(self, form: str) -> sp.csr_matrix:
+        """K = [[A, B^T], [B, -C]] unconstrained, [4nn, 4nn] (Sec. 5)."""
+        A = self.velocity_block(form)
+        B = self.divergence()
+        C = self.stabilisation()
+        return sp.bmat([[A, B.T], [B, -C]], format="csr")
+
+    # ------------------------------------------------------------------ boundary data
+    def node_ijk(self):
+        n1 = self.n + 1
+        idx = np.arange(self.nn)
+        return idx % n1, (idx // n1) % n1, idx // (n1 * n1)
+
+    def constrained(self) -> np.ndarray:
+        """Boolean [4nn]: True for velocity components fixed to zero by the boundary
+        conditions.  Dirichlet faces fix all components, free-slip faces the normal one;
+        a node on several faces takes the union.  Pressure is never constrained."""
+        i, j, k = self.node_ijk()
+        on = [i == 0, i == self.n, j == 0, j == self.n, k == 0, k == self.n]
+        mask = np.zeros((4, self.nn), dtype=bool)
+        for f in range(6):
+            axis = f // 2
+            if self.face[f] == DIRICHLET:
+                mask[:3, on[f]] = True
+            elif self.face[f] == FREESLIP:
+                mask[axis, on[f]] = True
+        return mask.ravel()
+
+    def has_pressure_nullspace(self) -> bool:
+        """Without a traction face the constant pressure is in the kernel of [B^T; -C]."""
+        return TRACTION not in self.face
+
+    def interface_nodes(self) -> np.ndarray:
+        """Boolean [nn]: nodes whose velocity test functions are not in H^1_0 of one
+        isoviscous subdomain - nodes touching cells of two or more viscosities, or lying on a
+        traction face - restricted to nodes with at least one free velocity component."""
+        n = self.n
+        mu = self.cell_mu.reshape(n, n, n)  # [k, j, i]
+        lo = np.full((n + 1,) * 3, np.inf)
+        hi = np.full((n + 1,) * 3, -np.inf)
+        for dk in (0, 1):
+            for dj in (0, 1):
+                for di in (0, 1):
+                    sl = (slice(dk, dk + n), slice(dj, dj + n), slice(di, di + n))
+                    lo[sl] = np.minimum(lo[sl], mu)
+                    hi[sl] = np.maximum(hi[sl], mu)
+        iface = (hi > lo).ravel()
+        i, j, k = self.node_ijk()
+        on = [i == 0, i == n, j == 0, j == n, k == 0, k == n]
+        for f in range(6):
+            if self.face[f] == TRACTION:
+                iface |= on[f]
+        free = ~self.constrained().reshape(4, self.nn)[:3].all(axis=0)
+        return iface & free
+
+    def rhs(self, f_nodal: np.ndarray = None, f_cell: np.ndarray = None) -> np.ndarray:
+        """Right-hand side [4nn] for a forcing given either at the nodes (f_nodal [3, nn])
+        or as a constant per hexahedral cell (f_cell [3, n^3]).
+
+        Nodal forcing: velocity rows are the lumped mass times the nodal value; the pressure
+        rows take the PSPG term g_b = -sum_T tau_T int_T f_h . grad lambda_b with f_h the P1
+        interpolant (exact integral: |T| times the vertex mean).  Cell forcing: velocity rows
+        are the exact integrals sum_T f_T |T| / 4 and g_b = -sum_T tau_T |T| f_T . grad
+        lambda_b.  Constrained rows are zero."""
+        b = np.zeros((4, self.nn))
+        if f_nodal is not None:
+            f = np.asarray(f_nodal, dtype=np.float64).reshape(3, self.nn)
+            b[:3] = self.lumped_mass()[None, :] * f
+            fT = f[:, self.tets].mean(axis=2).T  # [T, 3]
+        else:
+            fc = np.asarray(f_cell, dtype=np.float64).reshape(3, -1)
+            fT = fc[:, self.tet_cell].T
+            for c in range(3):
+                np.add.at(b[c], self.tets.ravel(), np.repeat(fT[:, c] * self.vol / 4.0, 4))
+        contrib = -np.einsum("t,td,tbd->tb", self.tau_T * self.vol, fT, self.grad)
+        np.add.at(b[3], self.tets.ravel(), contrib.ravel())
+        b = b.ravel()
+        b[self.constrained()] = 0.0
+        return b
+
+
+def masked(K: sp.spmatrix, constrained: np.ndarray) -> sp.csr_matrix:
+    """D K D with D the diagonal 0/1 matrix of free DoFs: rows and columns of constrained
+    DoFs set to zero, so K x on vectors that are zero at constrained DoFs gives the free
+    rows of K_ff x_f and zeros elsewhere."""
+    d = sp.diags((~constrained).astype(np.float64))
+    return (d @ K @ d).tocsr()

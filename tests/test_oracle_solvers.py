@@ -1,0 +1,157 @@
+"""Pins for the oracle's solvers (no GPU): convergence to exact solutions, the paper's
+qualitative results, and algebraic properties of the smoother, V-cycle and FGMRES."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import solvers as S
+from oracle.forms import DIRICHLET, Discretisation
+from oracle.solvers import Hierarchy, Level, fgmres, vcycle_preconditioner
+from paper_1604_07994_gb300 import workloads as W
+
+
+def _layer(n):
+    """A stiff layer z > 1/2 (mu = 10 over mu = 1), no-slip walls, manufactured solution."""
+    return W.inclusion_problem(n, 4, [((0.0, 1.0), (0.0, 1.0), (0.5, 1.0))], 10.0, 1.0, seed=0)
+
+
+def _nodal_exact_velocity(p, xyz):
+    n = p.n
+    cm = p.cell_mu()
+    idx = np.minimum((xyz * n).astype(int), n - 1)
+    mu_at = cm[idx[:, 2], idx[:, 1], idx[:, 0]]
+    return np.stack(p.exact(xyz[:, 0], xyz[:, 1], xyz[:, 2], mu_at)[:3])
+
+
+@pytest.mark.parametrize("form", ["tr", "sym", "grad"])
+def test_manufactured_velocity_converges_at_second_order(form):
+    """O(h^2) velocity L2 convergence on a manufactured piecewise solution satisfying the
+    interface conditions (the paper's tables report rates near 2 for consistent forms).  The
+    exact velocity has zero gradient on the interface, so all three forms are consistent."""
+    errs = []
+    for n in (8, 16):
+        p = _layer(n)
+        H = Hierarchy(n, 4, p.cell_mu().ravel(), p.face, form)
+        L = H.levels[0]
+        b = L.disc.rhs(p.nodal_forcing())
+        x = L.direct(b)
+        ue = _nodal_exact_velocity(p, L.disc.xyz)
+        m = L.disc.lumped_mass()
+        uh = x[: 3 * L.nn].reshape(3, -1)
+        errs.append(np.sqrt(np.sum(m * (uh - ue) ** 2) / np.sum(m * ue ** 2)))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate >= 1.8, (form, errs, rate)
+
+
+def _couette_error(n, form, mu1=1.0, mu2=1e-3):
+    """Couette flow of Sec. 4.2.2 shifted to the unit cube (interface y = 1/2):
+    u = (1/2 (1 - x^2), x (y - 1/2), 0), f = (3 mu, 0, 0), exact Dirichlet data."""
+    c = (np.arange(n) + 0.5) / n
+    _, Y, _ = np.meshgrid(c, c, c, indexing="ij")
+    cmu = np.where(Y < 0.5, mu1, mu2).ravel()
+    d = Discretisation(n, cmu, (DIRICHLET,) * 6)
+    fc = np.zeros((3, n ** 3))
+    fc[0] = 3.0 * cmu
+    b = d.rhs(f_cell=fc)
+    x, y, _ = d.xyz.T
+    ue = np.stack([0.5 * (1.0 - x ** 2), x * (y - 0.5), 0.0 * x])
+    con = d.constrained()
+    xD = np.zeros(4 * d.nn)
+    xD[: 3 * d.nn] = ue.ravel()
+    xD[~con] = 0.0
+    L = Level(n, cmu, (DIRICHLET,) * 6, form)
+    rhs = b - d.saddle(form) @ xD
+    rhs[con] = 0.0
+    xs = L.direct(rhs) + xD
+    m = d.lumped_mass()
+    uh = xs[: 3 * d.nn].reshape(3, -1)
+    return np.sqrt(np.sum(m * (uh - ue) ** 2) / np.sum(m * ue ** 2))
+
+
+def test_couette_consistent_forms_converge_gradient_form_stalls():
+    """Sec. 4.2.2 / Tables 2-7: a_tr and a_sym converge to the exact interface solution while
+    the gradient form converges to a different one (its error stops decreasing).  With a
+    continuous P1 pressure the jump [p] = 2x[mu] is not representable, so the consistent forms
+    converge below second order here; the pin is on the qualitative split."""
+    e = {f: [_couette_error(n, f) for n in (8, 16)] for f in ("tr", "sym", "grad")}
+    for f in ("tr", "sym"):
+        assert np.log2(e[f][0] / e[f][1]) >= 1.2, (f, e[f])
+    assert np.log2(e["grad"][0] / e["grad"][1]) <= 0.6, e["grad"]
+    assert e["grad"][1] > 2.0 * e["tr"][1]
+
+
+def test_dense_and_sparse_direct_solves_agree(monkeypatch):
+    p = W.cube_inclusion(8, 4)
+    L1 = Level(8, p.cell_mu().ravel(), p.face, "tr")
+    b = L1.disc.rhs(p.nodal_forcing())
+    x1 = L1.direct(b)
+    monkeypatch.setattr(S, "DENSE_LIMIT", 10)
+    L2 = Level(8, p.cell_mu().ravel(), p.face, "tr")
+    x2 = L2.direct(b)
+    assert np.linalg.norm(x1 - x2) <= 1e-10 * np.linalg.norm(x1)
+    r = L1.residual(x1, b)
+    assert np.linalg.norm(r[L1.free]) <= 1e-12 * np.linalg.norm(b)
+    w = L1.disc.pressure_weights()
+    assert abs(np.dot(w, x1[3 * L1.nn:])) <= 1e-12 * np.abs(x1).max()
+
+
+def test_single_level_cycle_is_the_direct_solve():
+    p = W.cube_inclusion(4, 4)
+    H = Hierarchy(4, 4, p.cell_mu().ravel(), p.face, "tr")
+    b = H.levels[0].disc.rhs(p.nodal_forcing())
+    x = H.vcycle(np.zeros_like(b), b)
+    assert np.array_equal(x, H.levels[0].direct(b))
+
+
+@pytest.mark.parametrize("form", ["tr", "sym"])
+def test_discrete_solution_is_a_fixed_point_of_the_smoother(form):
+    """Eq. (Uzawa_smooth) is consistent: both updates vanish at the discrete solution."""
+    p = W.cube_inclusion(8, 4)
+    L = Level(8, p.cell_mu().ravel(), p.face, form)
+    b = L.disc.rhs(p.nodal_forcing())
+    x = L.direct(b)
+    y = x.copy()
+    L.uzawa(y, b)
+    assert np.abs(y - x).max() <= 1e-9 * np.abs(x).max()
+
+
+@pytest.mark.parametrize("form", ["tr", "sym"])
+def test_vcycle_contracts_on_the_papers_columns_problem(form):
+    """Sec. 5 runs the V_var(3,3) Uzawa multigrid on the viscosity-columns problem and
+    measures asymptotic rates of 0.24 to 0.30 (Table timeANDconv).  Here, at n = 16 with a
+    4^3 coarsest grid, the rate stays well below one as well."""
+    p = W.viscosity_columns(16, 4)
+    H = Hierarchy(16, 4, p.cell_mu().ravel(), p.face, form)
+    b = H.levels[0].disc.rhs(p.nodal_forcing())
+    x, hist = H.solve(b, rtol=1e-10, maxit=30)
+    rho = (hist[-1] / hist[-4]) ** (1.0 / 3.0)
+    assert hist[-1] <= 1e-10 * np.linalg.norm(b[H.levels[0].free])
+    assert rho < 0.5, rho
+
+
+@pytest.mark.parametrize("coarse_form", [None, "sym"])
+def test_fgmres_vcycle_reaches_the_direct_solution_at_high_contrast(coarse_form):
+    """Floating stiff boxes (mu ratio 1e4): a_tr is indefinite (Sec. 3) and plain Uzawa
+    multigrid diverges, but FGMRES preconditioned by the V-cycle reaches the direct solution."""
+    p = W.three_boxes(16, 8, contrast=1e4)
+    H = Hierarchy(16, 8, p.cell_mu().ravel(), p.face, "tr", coarse_form=coarse_form)
+    L = H.levels[0]
+    b = L.disc.rhs(p.nodal_forcing())
+    x, hist = fgmres(L.K, vcycle_preconditioner(H), b, L.free, rtol=1e-12, restart=60, maxit=120)
+    assert hist[-1] <= 1e-12 * np.linalg.norm(b[L.free])
+    xd = L.direct(b)
+    w = L.disc.pressure_weights()
+    x[3 * L.nn:] -= np.dot(w, x[3 * L.nn:]) / w.sum()
+    assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+def test_fgmres_solves_a_small_system_exactly():
+    """With restart >= dimension, (F)GMRES terminates with the exact solution; checked against
+    numpy's dense solve on a nonsymmetric system with a Jacobi preconditioner."""
+    rng = np.random.Generator(np.random.PCG64(7))
+    n = 40
+    A = sp.csr_matrix(rng.standard_normal((n, n)) + 8.0 * np.eye(n))
+    b = rng.standard_normal(n)
+    d = A.diagonal()
+    x, hist = fgmres(A, lambda v: v / d, b, np.ones(n, dtype=bool), rtol=1e-13, restart=n)
+    assert np.linalg.norm(x - np.linalg.solve(A.toarray(), b)) <= 1e-11 * np.linalg.norm(x)
