@@ -1,0 +1,183 @@
+/*
+ * sdx.h - C ABI of the GB300 library for the decoupled (interface-strain) Stokes operator of
+ * Huber, Ruede, Waluga and Wohlmuth, "Highly sparse surface couplings for subdomain-wise
+ * isoviscous Stokes finite element discretizations" (arXiv:1604.07994), and the all-at-once
+ * Uzawa multigrid built on it.
+ *
+ * Discretisation (paper Sec. 4-5): unit cube, n^3 hexahedral cells each split into six Kuhn
+ * tetrahedra, equal-order P1-P1 velocity/pressure with pressure stabilisation
+ * C = sum_T tau_T (grad p, grad q)_T, tau_T = beta h^2 / mu_T.  The saddle system is
+ *     [ A  B^T ] [u]   [f]
+ *     [ B  -C  ] [p] = [g]           (Sec. 5, first display)
+ * where A comes from one of three bilinear forms:
+ *     SDX_FORM_DECOUPLED  a_tr  = a_sym - (mu div u, div v)    (Sec. 2, eq. newbil)
+ *     SDX_FORM_STRAIN     a_sym = (2 mu sym grad u, sym grad v) (Sec. 1, eq. standard)
+ *     SDX_FORM_GRADIENT   (mu grad u, grad v)                   (Sec. 4, inconsistent control)
+ * The decoupled form is applied as in Sec. 2.2, eq. (equivalence-stencil): a mu-weighted
+ * 7-point Laplacian per velocity component on every row, plus the strain cross-couplings
+ * only on rows of nodes that touch two viscosities or a traction face.
+ *
+ * Vectors ("SoA vectors") are four contiguous components u_x, u_y, u_z, p of (n+1)^3
+ * doubles each, node (i,j,k) at index i + (n+1)*(j + (n+1)*k).  Velocity components fixed by
+ * the boundary conditions ("constrained") must be zero on input and are written as zero.
+ * Unless stated otherwise, vector pointers are DEVICE pointers owned by the caller, and every
+ * call is asynchronous on the given CUDA stream (NULL = legacy default stream); the library
+ * allocates its own work buffers in sdx_create and frees them in sdx_destroy.
+ *
+ * Every function returns SDX_OK (0) or a negative error code; sdx_last_error() gives a
+ * message for the calling thread's last failure.  No C++ exception crosses this interface.
+ */
+#ifndef SDX_H
+#define SDX_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes. */
+#define SDX_OK 0
+#define SDX_EINVAL (-1)     /* invalid argument (sizes, null pointers, viscosities, ...) */
+#define SDX_ENOMEM (-2)     /* a device or host allocation failed; nothing leaked */
+#define SDX_ENONFINITE (-3) /* a NaN or Inf appeared in a residual norm */
+#define SDX_ENOCONV (-4)    /* maxit reached without meeting rtol; x holds the last iterate */
+#define SDX_ECUDA (-5)      /* a CUDA runtime call failed */
+#define SDX_ESINGULAR (-6)  /* the coarsest-grid matrix could not be factorised */
+
+/* Boundary face types (Sec. 1, eq. boundary).  Faces are ordered -x, +x, -y, +y, -z, +z. */
+#define SDX_FACE_DIRICHLET 0 /* u = 0 */
+#define SDX_FACE_FREESLIP 1  /* u.n = 0, zero tangential traction */
+#define SDX_FACE_TRACTION 2  /* sigma(u,p) n = 0 (natural) */
+
+/* Bilinear forms for the velocity block. */
+#define SDX_FORM_DECOUPLED 0
+#define SDX_FORM_STRAIN 1
+#define SDX_FORM_GRADIENT 2
+
+/* Arithmetic of the multigrid cycle.  The outer residual, the solution update and the
+ * coarsest-grid solve are always FP64. */
+#define SDX_PREC_FP64 0
+#define SDX_PREC_FP32_REFINED 1
+
+/* Outer iteration of sdx_solve. */
+#define SDX_OUTER_VCYCLE 0 /* repeated V-cycles (Sec. 5) */
+#define SDX_OUTER_FGMRES 1 /* flexible GMRES(restart) right-preconditioned by one V-cycle */
+
+typedef struct sdx_hier* sdx_hier_t; /* opaque, library-owned hierarchy */
+
+typedef struct {
+    int n;                  /* cells per side on the finest grid; n = n_coarse * 2^k, k >= 0 */
+    int n_coarse;           /* cells per side on the coarsest grid (>= 2); every viscosity
+                               interface must lie on a plane of that grid */
+    const uint8_t* cell_id; /* HOST array of n^3 subdomain ids, cell (i,j,k) at
+                               i + n*(j + n*k); ids must be < n_mu (and < 255) */
+    const double* mu;       /* HOST viscosity table indexed by id, all finite and > 0 */
+    int n_mu;               /* entries in mu, 1..255 */
+    int face[6];            /* SDX_FACE_* for -x, +x, -y, +y, -z, +z */
+    int form;               /* SDX_FORM_* on the finest level */
+    int coarse_form;        /* SDX_FORM_* on the coarser levels, or -1 for "same as form".
+                               (Sec. 5 swaps a_tr for a_sym on the coarse grid.) */
+    int prec;               /* SDX_PREC_* for sdx_vcycle and sdx_solve */
+    double pspg_beta;       /* stabilisation constant beta (> 0); 1/12 is the default used
+                               throughout this library's tests */
+} sdx_desc;
+
+typedef struct {
+    int iterations; /* V-cycles applied (each FGMRES iteration applies one) */
+    int restarts;   /* FGMRES restarts (0 for SDX_OUTER_VCYCLE) */
+    double res0;    /* ||b - K x0||_2 over free DoFs */
+    double res;     /* final ||b - K x||_2 */
+    double bnorm;   /* ||b||_2 */
+    int status;     /* same value as the call's return code */
+} sdx_stats;
+
+/* Build the grid hierarchy n, n/2, ..., n_coarse: cell viscosities, boundary masks,
+ * interface-row lists, device work buffers (library-owned) and the dense FP64 inverse of the
+ * coarsest-grid saddle matrix (bordered by the pressure-mean row int q/mu = 0 when no face is
+ * a traction face).  Synchronous.  Paper: Sec. 4.2.3 (mesh), Sec. 5 (direct coarse solve).
+ * Errors: SDX_EINVAL for bad sizes/ids/viscosities or interfaces not resolved on the
+ * coarsest grid, SDX_ENOMEM, SDX_ESINGULAR, SDX_ECUDA.  On error *out is set to NULL. */
+int sdx_create(const sdx_desc* desc, sdx_hier_t* out);
+
+/* Release every buffer of the hierarchy.  Synchronises the device first.  NULL is a no-op. */
+int sdx_destroy(sdx_hier_t h);
+
+/* Number of levels, and nodes / free DoFs of one level (0 = finest). */
+int sdx_levels(sdx_hier_t h, int* levels);
+int sdx_level_size(sdx_hier_t h, int level, int* n, int64_t* nodes, int64_t* free_dofs);
+
+/* Host query: mask[4*(n+1)^3] set to 1 at constrained DoFs of the level, 0 elsewhere. */
+int sdx_constraint_mask(sdx_hier_t h, int level, uint8_t* mask_host);
+
+/* Host query: iface[(n+1)^3] set to 1 at interface rows (nodes that get the strain
+ * cross-couplings in the decoupled form, Sec. 2.2), 0 elsewhere. */
+int sdx_interface_mask(sdx_hier_t h, int level, uint8_t* iface_host);
+
+/* y = K x on one level (device SoA vectors of that level's size), with the level's form.
+ * Paper: Sec. 2.2 eq. (equivalence-stencil) for the decoupled form; Sec. 5 saddle matrix. */
+int sdx_apply(sdx_hier_t h, int level, const double* x, double* y, void* stream);
+
+/* r = b - K x on one level. */
+int sdx_residual(sdx_hier_t h, int level, const double* b, const double* x, double* r,
+                 void* stream);
+
+/* Right-hand side of the finest level from nodal forcing f (device, three components of
+ * (n+1)^3): velocity rows m_b f(x_b) with the lumped mass m_b = int lambda_b; pressure rows
+ * the stabilisation term g_b = -sum_T tau_T int_T f_h . grad lambda_b (f_h: P1 interpolant).
+ * Constrained rows are zero. */
+int sdx_rhs(sdx_hier_t h, const double* f_nodal, double* b, void* stream);
+
+/* One Uzawa smoothing step (Sec. 5, eq. Uzawa_smooth) on one level, in place on x:
+ * symmetric red-black Gauss-Seidel on A (colours red, black, red; couplings between
+ * velocity components of same-coloured nodes taken from the values before the colour pass),
+ * then forward red-black Gauss-Seidel on C p = B u - g with relaxation 0.3.  FP64. */
+int sdx_uzawa(sdx_hier_t h, int level, const double* b, double* x, void* stream);
+
+/* One colour pass of the Uzawa smoother on one level, in place on x (FP64): which = 0 is
+ * the velocity Gauss-Seidel pass on A u = f - B^T p over nodes of the given colour
+ * (0: i+j+k even, 1: odd), which = 1 the relaxed pressure pass on C p = B u - g.  sdx_uzawa
+ * is velocity passes 0, 1, 0 followed by pressure passes 0, 1.  Paper: Sec. 5. */
+int sdx_smooth_pass(sdx_hier_t h, int level, int which, int colour, const double* b, double* x,
+                    void* stream);
+
+/* Transfers between level l (fine) and l+1 (coarse), standard nested P1 operators:
+ * sdx_restrict writes b_coarse = P^T r_fine; sdx_prolong_add does x_fine += P e_coarse.
+ * Constrained DoFs are masked on both levels.  FP64. */
+int sdx_restrict(sdx_hier_t h, int level, const double* r_fine, double* b_coarse, void* stream);
+int sdx_prolong_add(sdx_hier_t h, int level, const double* e_coarse, double* x_fine,
+                    void* stream);
+
+/* One variable V-cycle (V_var(3,3): 3 + 2k pre- and post-smoothing steps k levels below the
+ * finest) on the finest level, in place on x, in the hierarchy's precision.  FP32 mode runs
+ * the cycle on r = b - K x in FP32 and adds the correction in FP64.  Paper: Sec. 5. */
+int sdx_vcycle(sdx_hier_t h, const double* b, double* x, void* stream);
+
+/* Solve K x = b to ||b - K x||_2 <= rtol ||b||_2 (free DoFs), starting from the x passed in.
+ * outer: SDX_OUTER_VCYCLE or SDX_OUTER_FGMRES (restart = Krylov basis size, >= 1; ignored
+ * for V-cycles).  Synchronises the stream once per iteration to test convergence.  stats may
+ * be NULL.  Returns SDX_ENOCONV if maxit iterations did not meet rtol, SDX_ENONFINITE if a
+ * residual norm was NaN/Inf (x is then the last finite iterate or garbage, stats filled). */
+int sdx_solve(sdx_hier_t h, const double* b, double* x, double rtol, int maxit, int outer,
+              int restart, sdx_stats* stats, void* stream);
+
+/* As sdx_solve, but b_host and x_host are HOST arrays (pinned or pageable): copies b and x
+ * to library buffers, solves, copies x back, and synchronises the stream before returning. */
+int sdx_solve_host(sdx_hier_t h, const double* b_host, double* x_host, double rtol, int maxit,
+                   int outer, int restart, sdx_stats* stats, void* stream);
+
+/* Number of CUDA kernels this library has launched in the process so far (all
+ * hierarchies, all threads); used to count the kernels of a timed region. */
+int64_t sdx_kernel_launches(void);
+
+/* Message describing the calling thread's last error (never NULL). */
+const char* sdx_last_error(void);
+
+/* Static description of an error code (never NULL). */
+const char* sdx_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SDX_H */

@@ -222,6 +222,102 @@ class Discretisation:
         return b
 
 
+def sampled_rows(n, cell_mu, face, form, x, nodes, beta: float = PSPG_BETA):
+    """(K x) at selected nodes only, for grids too large to assemble: the rows of the given
+    nodes are summed over the tetrahedra of their patches with the same element integrals as
+    the global assembly (generic P1 geometry), the constrained rows set to zero.
+
+    cell_mu: [n^3] cell viscosities; x: [4 (n+1)^3] SoA vector (zero at constrained DoFs);
+    nodes: node indices.  Returns [4, len(nodes)]."""
+    n1 = n + 1
+    nn = n1 ** 3
+    cell_mu = np.asarray(cell_mu, dtype=np.float64).ravel()
+    x = np.asarray(x, dtype=np.float64).reshape(4, nn)
+    xyz_all = None
+    out = np.zeros((4, len(nodes)))
+    from .mesh import PERMS
+    h = 1.0 / n
+    for t, b in enumerate(nodes):
+        bi, bj, bk = b % n1, (b // n1) % n1, b // (n1 * n1)
+        tets, cells = [], []
+        for dk in (-1, 0):
+            for dj in (-1, 0):
+                for di in (-1, 0):
+                    ci, cj, ck = bi + di, bj + dj, bk + dk
+                    if min(ci, cj, ck) < 0 or max(ci, cj, ck) >= n:
+                        continue
+                    for s in PERMS:
+                        off = [0, 0, 0]
+                        verts = [ci + n1 * (cj + n1 * ck)]
+                        for ax in s:
+                            off[ax] += 1
+                            verts.append(ci + off[0] + n1 * (cj + off[1] + n1 * (ck + off[2])))
+                        if b in verts:
+                            tets.append(verts)
+                            cells.append(ci + n * (cj + n * ck))
+        tets = np.array(tets)
+        cells = np.array(cells)
+        ijk = np.stack([tets % n1, (tets // n1) % n1, tets // (n1 * n1)], axis=2)
+        xyz = ijk * h
+        M = np.concatenate([np.ones(xyz.shape[:2] + (1,)), xyz], axis=2)
+        C = np.linalg.inv(M)
+        grad = np.transpose(C[:, 1:, :], (0, 2, 1))
+        vol = np.abs(np.linalg.det(M)) / 6.0
+        mu_T = cell_mu[cells]
+        tau_T = beta * h ** 2 / mu_T
+        loc = np.array([list(tv).index(b) for tv in tets])  # b's vertex in each tet
+        gb = grad[np.arange(len(tets)), loc]  # [T, 3]
+        E, G = _sym_basis(grad)
+        Eb = E[np.arange(len(tets)), loc]  # [T, j, k, l]
+        Gb = G[np.arange(len(tets)), loc]
+        U = x[:3][:, tets]  # [i, T, a]
+        Pv = x[3][tets]  # [T, a]
+        w = mu_T * vol
+        # sym grad u_h and grad u_h per tet
+        Gu = np.einsum("iTa,Tad->Tid", U, grad)  # d_d u_i
+        Eu = 0.5 * (Gu + np.transpose(Gu, (0, 2, 1)))
+        divu = np.einsum("Tii->T", Gu)
+        if form == "sym":
+            au = 2.0 * np.einsum("T,Tkl,Tjkl->j", w, Eu, Eb)
+        elif form == "tr":
+            au = 2.0 * np.einsum("T,Tkl,Tjkl->j", w, Eu, Eb) - np.einsum("T,T,Tj->j", w, divu, gb)
+        elif form == "grad":
+            au = np.einsum("T,Tkl,Tjkl->j", w, Gu, Gb)
+        else:
+            raise ValueError(form)
+        btp = -np.einsum("T,Tj,T->j", vol / 4.0, gb, Pv.sum(axis=1))
+        bu = -np.sum(vol / 4.0 * divu)
+        gp = np.einsum("Ta,Tad->Td", Pv, grad)
+        cp = np.sum(tau_T * vol * np.einsum("Td,Td->T", gp, gb))
+        out[:3, t] = au + btp
+        out[3, t] = bu - cp
+    # constrained rows
+    d = _BoundaryOnly(n, face)
+    con = d.constrained_nodes(np.asarray(nodes))
+    out[:3][con] = 0.0
+    return out
+
+
+class _BoundaryOnly:
+    """Constraint flags of selected nodes without building the mesh (same rule as
+    Discretisation.constrained)."""
+
+    def __init__(self, n, face):
+        self.n, self.face = n, tuple(int(f) for f in face)
+
+    def constrained_nodes(self, nodes):
+        n1 = self.n + 1
+        i, j, k = nodes % n1, (nodes // n1) % n1, nodes // (n1 * n1)
+        on = [i == 0, i == self.n, j == 0, j == self.n, k == 0, k == self.n]
+        mask = np.zeros((3, nodes.size), dtype=bool)
+        for f in range(6):
+            if self.face[f] == DIRICHLET:
+                mask[:, on[f]] = True
+            elif self.face[f] == FREESLIP:
+                mask[f // 2, on[f]] = True
+        return mask
+
+
 def masked(K: sp.spmatrix, constrained: np.ndarray) -> sp.csr_matrix:
     """D K D with D the diagonal 0/1 matrix of free DoFs: rows and columns of constrained
     DoFs set to zero, so K x on vectors that are zero at constrained DoFs gives the free

@@ -1,0 +1,137 @@
+// Internal declarations of the sdx library: level data, kernel launchers, hierarchy.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace sdx {
+
+enum Form { FORM_TR = 0, FORM_SYM = 1, FORM_GRAD = 2 };
+
+// Per-node information word.
+constexpr uint16_t INFO_CX = 1;        // u_x constrained
+constexpr uint16_t INFO_CY = 2;        // u_y constrained
+constexpr uint16_t INFO_CZ = 4;        // u_z constrained
+constexpr uint16_t INFO_SPECIAL = 8;   // not (interior node with 8 cells of one viscosity)
+constexpr uint16_t INFO_IFACE = 16;    // interface row: decoupled form adds cross-couplings
+constexpr uint8_t CELL_OUTSIDE = 255;  // id of the ghost cells around the domain
+
+constexpr double OMEGA = 0.3;          // pressure Gauss-Seidel relaxation (Sec. 5)
+
+// Read-only view of one level as seen by kernels, for arithmetic type T.
+template <typename T>
+struct LevelView {
+    int n;              // cells per side
+    int n1;             // nodes per side (n + 1)
+    long long nn;       // nodes (n+1)^3
+    long long s1, s2;   // node strides for +y and +z
+    int P;              // cells per side of the padded cell array (n + 2)
+    T h;                // 1 / n
+    const uint8_t* cid;     // padded cell ids [(n+2)^3], CELL_OUTSIDE in the ghost layer
+    const uint16_t* info;   // [nn]
+    const T* mu;            // viscosity table [256], mu[CELL_OUTSIDE] = 0
+    const T* tau;           // stabilisation weight beta h^2 / mu [256], 0 for outside
+};
+
+// Device buffers of one level.
+struct Level {
+    int n = 0;
+    long long nn = 0;
+    int form = FORM_TR;
+    double h = 0;
+    std::vector<uint8_t> cid_host;    // padded
+    std::vector<uint16_t> info_host;
+    uint8_t* cid = nullptr;
+    uint16_t* info = nullptr;
+    double* tau_d = nullptr;
+    float* tau_f = nullptr;
+    // special node lists (int32 node indices)
+    int* spec_all = nullptr;  int n_spec_all = 0;
+    int* spec_vel[2] = {nullptr, nullptr};  int n_spec_vel[2] = {0, 0};
+    int* spec_pre[2] = {nullptr, nullptr};  int n_spec_pre[2] = {0, 0};
+    long long free_dofs = 0;
+    // work vectors (4 components unless noted)
+    double* x = nullptr;  double* b = nullptr;  double* r = nullptr;
+    float* x32 = nullptr; float* b32 = nullptr; float* r32 = nullptr;
+    double* sym_tmp = nullptr;  float* sym_tmp32 = nullptr;   // 3 components (strain form)
+    double* spec_tmp = nullptr; float* spec_tmp32 = nullptr;  // 3 * max special colour count
+};
+
+struct Coarse {
+    int nf = 0;                 // free DoFs
+    int* free_idx = nullptr;    // [nf] SoA index of each free DoF
+    double* kinv = nullptr;     // [nf * nf] row-major inverse (top-left block if bordered)
+    double* bc = nullptr;       // [nf]
+    double* xc = nullptr;       // [nf]
+};
+
+struct Hier {
+    int n = 0, n_coarse = 0, prec = 0;
+    int form = 0, coarse_form = 0;
+    double beta = 1.0 / 12.0;
+    int face[6] = {0, 0, 0, 0, 0, 0};
+    bool nullspace = false;
+    std::vector<double> mu_table;   // [256]
+    double* mu_d = nullptr;
+    float* mu_f = nullptr;
+    std::vector<Level> lv;
+    Coarse coarse;
+    // scalar scratch for reductions
+    double* red_part = nullptr;  int red_blocks = 0;
+    double* scal = nullptr;      // device scalars [256]
+    double* scal_host = nullptr; // pinned mirror [256]
+    // outer-iteration buffers (finest level, FP64)
+    double* r0 = nullptr;   double* xh = nullptr;  double* bh = nullptr;
+    std::vector<double*> V, Z;
+    int krylov_m = 0;
+};
+
+template <typename T>
+LevelView<T> view(const Hier& H, int l);
+
+// ---------------------------------------------------------------- kernel launchers
+template <typename T>
+void launch_apply(const Hier& H, int l, const T* x, T* y, const T* b, cudaStream_t s);
+template <typename T>
+void launch_uzawa(const Hier& H, int l, T* x, const T* b, cudaStream_t s);
+template <typename T>
+void launch_smooth_pass(const Hier& H, int l, int which, int colour, T* x, const T* b, cudaStream_t s);
+template <typename T>
+void launch_restrict(const Hier& H, int l, const T* rf, T* bc, cudaStream_t s);
+template <typename T>
+void launch_prolong_add(const Hier& H, int l, const T* ec, T* xf, cudaStream_t s);
+void launch_rhs(const Hier& H, const double* f, double* b, cudaStream_t s);
+
+// vector helpers over count elements
+template <typename T>
+void vec_zero(T* v, long long count, cudaStream_t s);
+void vec_axpy_dev(double* y, const double* x, const double* alpha_dev, double sign, long long count,
+                  cudaStream_t s);
+void vec_axpy(double* y, const double* x, double alpha, long long count, cudaStream_t s);
+void vec_scale_dev(double* y, const double* x, const double* scal_dev, bool reciprocal,
+                   long long count, cudaStream_t s);
+void vec_copy(double* y, const double* x, long long count, cudaStream_t s);
+void vec_d2f(float* y, const double* x, const double* scal_dev, long long count, cudaStream_t s);
+void vec_f2d_add(double* y, const float* x, const double* scal_dev, long long count,
+                 cudaStream_t s);
+// dot(x, y) -> *out_dev (deterministic two-pass reduction)
+void vec_dot(const Hier& H, const double* x, const double* y, long long count, double* out_dev,
+             cudaStream_t s);
+// coarse solve on the coarsest level's vectors
+template <typename T>
+void launch_coarse_solve(const Hier& H, const T* b, T* x, cudaStream_t s);
+
+// Gauss-Jordan inverse with partial pivoting on the device; returns false if singular
+bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s);
+
+// kernel-launch counter (add the number of launches issued)
+void count_launches(long long k);
+long long launches_total();
+
+// error helper
+void set_error(const std::string& msg);
+
+}  // namespace sdx

@@ -1,0 +1,77 @@
+"""The C-ABI library builds, loads, and exports every entry point include/sdx.h declares
+(no GPU needed: nothing here launches a kernel)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+
+from tests._lib import ensure_built
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "sdx.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(sdx_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_documented_entry_points():
+    names = _declared()
+    for n in ("sdx_create", "sdx_destroy", "sdx_apply", "sdx_vcycle", "sdx_solve", "sdx_strerror"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ensure_built()
+    for name in _declared():
+        assert hasattr(lib, name), name
+    from paper_1604_07994_gb300 import sdx
+    assert set(sdx.EXPORTED) == set(_declared())
+
+
+def test_exports_are_plain_c_symbols():
+    from paper_1604_07994_gb300 import sdx
+    ensure_built()
+    out = subprocess.run(["nm", "-D", "--defined-only", sdx.LIB_PATH], capture_output=True, text=True).stdout
+    syms = {line.split()[-1] for line in out.splitlines() if line.strip()}
+    for name in _declared():
+        assert name in syms, name  # unmangled: extern "C"
+
+
+def test_strerror_and_argument_validation_without_a_device():
+    from paper_1604_07994_gb300 import sdx
+    lib = ensure_built()
+    assert lib.sdx_strerror(sdx.EINVAL) == b"invalid argument"
+    assert lib.sdx_strerror(12345) == b"unknown error"
+    # a null descriptor is rejected before any CUDA call
+    h = ctypes.c_void_p()
+    assert lib.sdx_create(None, ctypes.byref(h)) == sdx.EINVAL
+    assert h.value is None
+    # host-side validation: n not n_coarse * 2^k, bad viscosity, out-of-range id
+    cells = np.zeros(6 ** 3, dtype=np.uint8)
+    mu = np.array([1.0, -2.0])
+    d = sdx.sdx_desc()
+    d.n, d.n_coarse = 6, 4
+    d.cell_id = cells.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    d.mu = mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_mu = 1
+    d.form, d.coarse_form, d.prec, d.pspg_beta = 0, -1, 0, 1.0 / 12
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert b"n_coarse" in lib.sdx_last_error()
+    d.n, d.n_coarse, d.n_mu = 8, 4, 2
+    cells8 = np.zeros(8 ** 3, dtype=np.uint8)
+    d.cell_id = cells8.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert b"viscosit" in lib.sdx_last_error()
+    mu_ok = np.array([1.0])
+    d.mu = mu_ok.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_mu = 1
+    cells8[5] = 3
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert b"cell id" in lib.sdx_last_error()
+    # null hierarchy handles
+    assert lib.sdx_apply(None, 0, None, None, None) == sdx.EINVAL
+    assert lib.sdx_destroy(None) == sdx.OK

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle on the same seeded
+inputs.  Tolerances: 1e-13 relative max-norm per FP64 operator apply and 1e-8 relative L2 per
+solve (the accuracy targets of this work); smoother, transfer and cycle steps, which add
+divisions and a dense coarse inverse, use 1e-12 / 1e-10 as stated in each test."""
+import numpy as np
+import pytest
+
+from tests._lib import ensure_built
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.forms import Discretisation, masked, sampled_rows  # noqa: E402
+from oracle.solvers import Hierarchy as OracleHierarchy  # noqa: E402
+from paper_1604_07994_gb300 import workloads as W  # noqa: E402
+
+APPLY_TOL = 1e-13
+SOLVE_TOL = 1e-8
+
+
+@pytest.fixture(scope="module")
+def sdx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    from paper_1604_07994_gb300 import sdx as mod
+    return mod
+
+
+def _problems():
+    rng = np.random.Generator(np.random.PCG64(11))
+    # 48 cells per side, coarse lattice 6 (not a power of two), three viscosity ids
+    ids = rng.integers(0, 3, (6, 6, 6)).astype(np.uint8)
+    ids = np.repeat(np.repeat(np.repeat(ids, 8, 0), 8, 1), 8, 2)
+    mixed = W.Problem(n=48, n_coarse=6, cell_id=ids, mu=np.array([1.0, 30.0, 0.05]),
+                      face=(0, 1, 2, 1, 0, 2), forcing=W.gaussian_blobs(5), name="mixed_48")
+    return {
+        "cube16": W.cube_inclusion(16, 4),
+        "boxes16": W.three_boxes(16, 8, contrast=1e4),
+        "layer16": W.top_layer(16, 8),
+        "columns16": W.viscosity_columns(16, 4),
+        "layers16": W.viscosity_layers(16, 4),
+        "mixed48": mixed,
+        "tiny2": W.Problem(n=2, n_coarse=2, cell_id=np.array([[[0, 1], [1, 0]], [[1, 1], [0, 0]]], dtype=np.uint8),
+                           mu=np.array([1.0, 7.0]), face=(2, 0, 1, 2, 0, 1), forcing=W.gaussian_blobs(1), name="tiny2"),
+    }
+
+
+PROBLEMS = _problems()
+
+
+def _masked_random(d, seed):
+    x = W.random_vector(d.n, seed).ravel()
+    x[d.constrained()] = 0.0
+    return x
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("form", ["tr", "sym", "grad"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_apply_matches_oracle(sdx, name, form):
+    p = PROBLEMS[name]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    K = masked(d.saddle(form), d.constrained())
+    H = sdx.Hierarchy.from_problem(p, form=form)
+    for seed in (1, 2):
+        x = _masked_random(d, seed)
+        y = _dev(np.zeros_like(x))
+        H.sdx_apply(0, _dev(x), y)
+        assert _relmax(_host(y), K @ x) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("name", ["cube16", "layer16", "mixed48", "tiny2"])
+def test_masks_match_oracle(sdx, name):
+    p = PROBLEMS[name]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    H = sdx.Hierarchy.from_problem(p)
+    assert np.array_equal(H.sdx_constraint_mask(0), d.constrained())
+    assert np.array_equal(H.sdx_interface_mask(0), d.interface_nodes())
+    n, nodes, free = H.sdx_level_size(0)
+    assert (n, nodes, free) == (p.n, d.nn, int((~d.constrained()).sum()))
+
+
+@pytest.mark.parametrize("name", ["cube16", "layer16", "mixed48"])
+def test_residual_and_rhs_match_oracle(sdx, name):
+    p = PROBLEMS[name]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    K = masked(d.saddle("tr"), d.constrained())
+    H = sdx.Hierarchy.from_problem(p)
+    f = p.nodal_forcing()
+    b = _dev(np.zeros(4 * d.nn))
+    H.sdx_rhs(_dev(f.ravel()), b)
+    bo = d.rhs(f)
+    assert _relmax(_host(b), bo) <= APPLY_TOL
+    x = _masked_random(d, 4)
+    r = _dev(np.zeros_like(x))
+    H.sdx_residual(0, _dev(bo), _dev(x), r)
+    assert _relmax(_host(r), bo - K @ x) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("form", ["tr", "sym"])
+@pytest.mark.parametrize("name", ["cube16", "boxes16", "layer16", "mixed48", "tiny2"])
+def test_uzawa_step_matches_oracle(sdx, name, form):
+    """One smoothing step (eq. Uzawa_smooth) from a random state, same colour order."""
+    p = PROBLEMS[name]
+    OH = OracleHierarchy(p.n, p.n, p.cell_mu().ravel(), p.face, form)
+    L = OH.levels[0]
+    H = sdx.Hierarchy.from_problem(p, form=form)
+    x = _masked_random(L.disc, 7)
+    b = _masked_random(L.disc, 8)
+    xd = _dev(x)
+    H.sdx_uzawa(0, _dev(b), xd)
+    L.uzawa(x, b)
+    assert _relmax(_host(xd), x) <= 1e-12
+
+
+@pytest.mark.parametrize("name", ["cube16", "layer16", "mixed48"])
+def test_transfers_match_oracle(sdx, name):
+    p = PROBLEMS[name]
+    OH = OracleHierarchy(p.n, p.n // 2, p.cell_mu().ravel(), p.face, "tr")
+    H = sdx.Hierarchy.from_problem(W.Problem(p.n, p.n // 2, p.cell_id, p.mu, p.face, p.forcing))
+    fine, coarse = OH.levels
+    rf = _masked_random(fine.disc, 9)
+    bc = _dev(np.zeros(4 * coarse.nn))
+    H.sdx_restrict(0, _dev(rf), bc)
+    assert _relmax(_host(bc), OH.P[0].T @ rf) <= APPLY_TOL
+    ec = _masked_random(coarse.disc, 10)
+    xf0 = _masked_random(fine.disc, 11)
+    xf = _dev(xf0)
+    H.sdx_prolong_add(0, _dev(ec), xf)
+    assert _relmax(_host(xf), xf0 + OH.P[0] @ ec) <= APPLY_TOL
+
+
+@pytest.mark.parametrize("form,coarse_form", [("tr", None), ("sym", None), ("tr", "sym")])
+@pytest.mark.parametrize("name", ["cube16", "columns16", "boxes16", "layer16"])
+def test_vcycle_matches_oracle(sdx, name, form, coarse_form):
+    """One V_var cycle from zero: smoother, residual, restriction, coarse solve (dense
+    inverse vs. LU: 1e-10), prolongation and post-smoothing in the oracle's order."""
+    p = PROBLEMS[name]
+    OH = OracleHierarchy(p.n, p.n_coarse, p.cell_mu().ravel(), p.face, form, coarse_form=coarse_form)
+    d = OH.levels[0].disc
+    b = d.rhs(p.nodal_forcing())
+    H = sdx.Hierarchy.from_problem(p, form=form, coarse_form=coarse_form)
+    xd = _dev(np.zeros_like(b))
+    H.sdx_vcycle(_dev(b), xd)
+    xo = OH.vcycle(np.zeros_like(b), b)
+    assert np.linalg.norm(_host(xd) - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+def _project(x, d):
+    w = d.pressure_weights()
+    x = x.copy()
+    x[3 * d.nn:] -= np.dot(w, x[3 * d.nn:]) / w.sum()
+    return x
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name,form,outer", [("cube16", "tr", 0), ("cube16", "sym", 0), ("boxes16", "tr", 1),
+                                             ("boxes16", "sym", 1), ("layer16", "tr", 1), ("columns16", "tr", 0)])
+def test_solve_matches_direct_solution(sdx, name, form, outer, prec):
+    p = PROBLEMS[name]
+    OH = OracleHierarchy(p.n, p.n_coarse, p.cell_mu().ravel(), p.face, form)
+    L = OH.levels[0]
+    b = L.disc.rhs(p.nodal_forcing())
+    xo = L.direct(b)
+    H = sdx.Hierarchy.from_problem(p, form=form, prec=prec)
+    xd = _dev(np.zeros_like(b))
+    st = H.sdx_solve(_dev(b), xd, rtol=1e-12, maxit=300, outer=outer, restart=40)
+    assert st["res"] <= 1e-12 * st["bnorm"]
+    x = _host(xd)
+    if L.nullspace:
+        x = _project(x, L.disc)
+    assert np.linalg.norm(x - xo) <= SOLVE_TOL * np.linalg.norm(xo)
+
+
+def test_solve_host_matches_device_solve(sdx):
+    p = PROBLEMS["cube16"]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    b = d.rhs(p.nodal_forcing())
+    H = sdx.Hierarchy.from_problem(p)
+    xd = _dev(np.zeros_like(b))
+    st1 = H.sdx_solve(_dev(b), xd, rtol=1e-9, outer=0)
+    xh = np.zeros_like(b)
+    st2 = H.sdx_solve_host(np.ascontiguousarray(b), xh, rtol=1e-9, outer=0)
+    assert st1["iterations"] == st2["iterations"]
+    assert np.array_equal(_host(xd), xh)
+
+
+def test_full_size_apply_sampled_rows(sdx):
+    """128^3 cells, three boxes with mu ratio 1e4 (the benchmark workload): sampled rows
+    of the GPU apply against the oracle's patch-wise row evaluation."""
+    p = W.three_boxes(128, 8, contrast=1e4)
+    cm = p.cell_mu().ravel()
+    nn = p.nodes
+    rng = np.random.Generator(np.random.PCG64(21))
+    H = sdx.Hierarchy.from_problem(p)
+    con = H.sdx_constraint_mask(0)
+    iface = np.flatnonzero(H.sdx_interface_mask(0))
+    x = W.random_vector(p.n, 12).ravel()
+    x[con] = 0.0
+    y = _dev(np.zeros_like(x))
+    H.sdx_apply(0, _dev(x), y)
+    yh = _host(y).reshape(4, nn)
+    nodes = np.concatenate([rng.integers(0, nn, 300), rng.choice(iface, 200), np.arange(0, 129 * 3)])
+    for form in ("tr",):
+        ys = sampled_rows(p.n, cm, p.face, form, x, nodes)
+        assert np.abs(ys - yh[:, nodes]).max() <= APPLY_TOL * np.abs(yh).max()
