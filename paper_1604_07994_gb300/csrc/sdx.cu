@@ -395,6 +395,8 @@ static void vcycle_rec(Hier& H, int l, T* x, const T* b, cudaStream_t s) {
     T* r = Buf<T>::r(L);
     launch_apply<T>(H, l, x, r, b, s);
     launch_restrict<T>(H, l, r, Buf<T>::b(Lc), s);
+    // the coarse-grid correction starts from zero (the coarsest solve overwrites anyway)
+    if (l + 1 < last) vec_zero<T>(Buf<T>::x(Lc), 4 * Lc.nn, s);
     vcycle_rec<T>(H, l + 1, Buf<T>::x(Lc), Buf<T>::b(Lc), s);
     launch_prolong_add<T>(H, l, Buf<T>::x(Lc), x, s);
     for (int i = 0; i < nu; ++i) launch_uzawa<T>(H, l, x, b, s);

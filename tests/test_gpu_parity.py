@@ -144,19 +144,36 @@ def test_transfers_match_oracle(sdx, name):
 
 
 @pytest.mark.parametrize("form,coarse_form", [("tr", None), ("sym", None), ("tr", "sym")])
-@pytest.mark.parametrize("name", ["cube16", "columns16", "boxes16", "layer16"])
+@pytest.mark.parametrize("name", ["cube16", "columns16", "boxes16", "layer16", "mixed48"])
 def test_vcycle_matches_oracle(sdx, name, form, coarse_form):
-    """One V_var cycle from zero: smoother, residual, restriction, coarse solve (dense
-    inverse vs. LU: 1e-10), prolongation and post-smoothing in the oracle's order."""
+    """Two consecutive V_var cycles from zero: smoother, residual, restriction, coarse solve
+    (dense inverse vs. LU: 1e-10), prolongation and post-smoothing in the oracle's order.
+    The second cycle checks that no level keeps state from the first."""
     p = PROBLEMS[name]
     OH = OracleHierarchy(p.n, p.n_coarse, p.cell_mu().ravel(), p.face, form, coarse_form=coarse_form)
     d = OH.levels[0].disc
     b = d.rhs(p.nodal_forcing())
     H = sdx.Hierarchy.from_problem(p, form=form, coarse_form=coarse_form)
     xd = _dev(np.zeros_like(b))
-    H.sdx_vcycle(_dev(b), xd)
-    xo = OH.vcycle(np.zeros_like(b), b)
-    assert np.linalg.norm(_host(xd) - xo) <= 1e-10 * np.linalg.norm(xo)
+    bd = _dev(b)
+    xo = np.zeros_like(b)
+    for _ in range(2):
+        H.sdx_vcycle(bd, xd)
+        OH.vcycle(xo, b)
+        assert np.linalg.norm(_host(xd) - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+def _reference_solution(OH, b):
+    """Oracle solution: direct LU when the system is small, otherwise the oracle's FGMRES +
+    V-cycle driven to a 1e-13 relative residual, near FP64's attainable accuracy (sparse LU
+    with partial pivoting fills in badly on the high-contrast strain systems)."""
+    from oracle import solvers as S
+    L = OH.levels[0]
+    if int(L.free.sum()) <= S.DENSE_LIMIT:
+        return L.direct(b)
+    x, hist = S.fgmres(L.K, S.vcycle_preconditioner(OH), b, L.free, rtol=1e-13, restart=60, maxit=600)
+    assert hist[-1] <= 3e-13 * np.linalg.norm(b[L.free])
+    return _project(x, L.disc) if L.nullspace else x
 
 
 def _project(x, d):
@@ -174,7 +191,7 @@ def test_solve_matches_direct_solution(sdx, name, form, outer, prec):
     OH = OracleHierarchy(p.n, p.n_coarse, p.cell_mu().ravel(), p.face, form)
     L = OH.levels[0]
     b = L.disc.rhs(p.nodal_forcing())
-    xo = L.direct(b)
+    xo = _reference_solution(OH, b)
     H = sdx.Hierarchy.from_problem(p, form=form, prec=prec)
     xd = _dev(np.zeros_like(b))
     st = H.sdx_solve(_dev(b), xd, rtol=1e-12, maxit=300, outer=outer, restart=40)
@@ -195,7 +212,7 @@ def test_solve_host_matches_device_solve(sdx):
     xh = np.zeros_like(b)
     st2 = H.sdx_solve_host(np.ascontiguousarray(b), xh, rtol=1e-9, outer=0)
     assert st1["iterations"] == st2["iterations"]
-    assert np.array_equal(_host(xd), xh)
+    assert np.array_equal(_host(xd), xh)  # deterministic: same bits from the same inputs
 
 
 def test_full_size_apply_sampled_rows(sdx):
