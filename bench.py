@@ -40,6 +40,10 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per side (workload size)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep"],
+                    help="sweep: only time the operator apply and smoother passes (profiling)")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="arithmetic of --mode sweep")
+    ap.add_argument("--form", default="tr", choices=["tr", "sym", "grad"])
     return ap.parse_args()
 
 
@@ -162,6 +166,9 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "sweep":
+        run_sweeps(args)
         return
     import torch
     ws, rank, local = dist_env()
@@ -340,6 +347,49 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
     if not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         out["cpu_baseline"] = oracle_sample()
     return out
+
+
+def run_sweeps(args):
+    """Per-sweep timing on the benchmark workload: operator apply, velocity and pressure
+    colour passes of the finest level, FP64 or FP32, one form."""
+    import torch
+    from paper_1604_07994_gb300 import sdx
+    from paper_1604_07994_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    prob = W.three_boxes(args.n, 8, contrast=1e4)
+    prec = sdx.PREC_FP64 if args.prec == "fp64" else sdx.PREC_FP32_REFINED
+    H = sdx.Hierarchy.from_problem(prob, form=args.form, prec=prec)
+    _, nn, free = H.sdx_level_size(0)
+    dt = torch.float64 if args.prec == "fp64" else torch.float32
+    con = torch.from_numpy(H.sdx_constraint_mask(0)).cuda()
+    x = torch.from_numpy(W.random_vector(args.n, 5).ravel()).cuda().to(dt)
+    bv = torch.from_numpy(W.random_vector(args.n, 6).ravel()).cuda().to(dt)
+    x[con] = 0
+    bv[con] = 0
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream()
+    if args.prec == "fp64":
+        ops = {"apply": lambda: H.sdx_apply(0, x, y),
+               "velocity_pass": lambda: H.sdx_smooth_pass(0, 0, 0, bv, x),
+               "pressure_pass": lambda: H.sdx_smooth_pass(0, 1, 0, bv, x)}
+    else:
+        ops = {"apply": lambda: H.sdx_apply_f32(0, x, y),
+               "velocity_pass": lambda: H.sdx_smooth_pass_f32(0, 0, 0, bv, x),
+               "pressure_pass": lambda: H.sdx_smooth_pass_f32(0, 1, 0, bv, x)}
+    w = 4 if args.prec == "fp32" else 8
+    bytes_per_node = {"apply": 8 * w, "velocity_pass": 7 * w + 2, "pressure_pass": 5.5 * w + 2}
+    res = {}
+    for _ in range(args.warmup):
+        for f in ops.values():
+            f()
+    torch.cuda.synchronize()
+    for name, f in ops.items():
+        ms = _time(f, args.steps, stream, torch)
+        rows = free if name == "apply" else (3 * nn / 2 if name == "velocity_pass" else nn / 2)
+        res[name] = {"ms": ms, "gdofs": rows / (ms * 1e-3) / 1e9,
+                     "algorithmic_gbs": bytes_per_node[name] * nn / (ms * 1e-3) / 1e9}
+    print(json.dumps({"mode": "sweep", "n": args.n, "prec": args.prec, "form": args.form, "nodes": nn,
+                      "free_dofs": free, "sweeps": res}), flush=True)
 
 
 if __name__ == "__main__":

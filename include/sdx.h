@@ -96,8 +96,10 @@ typedef struct {
  * interface-row lists, device work buffers (library-owned) and the dense FP64 inverse of the
  * coarsest-grid saddle matrix (bordered by the pressure-mean row int q/mu = 0 when no face is
  * a traction face).  Synchronous.  Paper: Sec. 4.2.3 (mesh), Sec. 5 (direct coarse solve).
- * Errors: SDX_EINVAL for bad sizes/ids/viscosities or interfaces not resolved on the
- * coarsest grid, SDX_ENOMEM, SDX_ESINGULAR, SDX_ECUDA.  On error *out is set to NULL. */
+ * The coarsest grid may have at most 12000 unknowns (n_coarse <= 13 or so), since its saddle
+ * matrix is inverted densely.
+ * Errors: SDX_EINVAL for bad sizes/ids/viscosities, interfaces not resolved on the coarsest
+ * grid or a coarsest grid too large, SDX_ENOMEM, SDX_ESINGULAR, SDX_ECUDA.  On error *out is set to NULL. */
 int sdx_create(const sdx_desc* desc, sdx_hier_t* out);
 
 /* Release every buffer of the hierarchy.  Synchronises the device first.  NULL is a no-op. */
@@ -140,6 +142,13 @@ int sdx_uzawa(sdx_hier_t h, int level, const double* b, double* x, void* stream)
  * is velocity passes 0, 1, 0 followed by pressure passes 0, 1.  Paper: Sec. 5. */
 int sdx_smooth_pass(sdx_hier_t h, int level, int which, int colour, const double* b, double* x,
                     void* stream);
+
+/* FP32 versions of sdx_apply and sdx_smooth_pass on FP32 SoA vectors (float, same layout):
+ * the arithmetic of the FP32 multigrid cycle used by SDX_PREC_FP32_REFINED.  They need a
+ * hierarchy created with prec = SDX_PREC_FP32_REFINED (SDX_EINVAL otherwise). */
+int sdx_apply_f32(sdx_hier_t h, int level, const float* x, float* y, void* stream);
+int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const float* b, float* x,
+                        void* stream);
 
 /* Transfers between level l (fine) and l+1 (coarse), standard nested P1 operators:
  * sdx_restrict writes b_coarse = P^T r_fine; sdx_prolong_add does x_fine += P e_coarse.

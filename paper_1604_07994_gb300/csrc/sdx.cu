@@ -181,6 +181,11 @@ static void build_coarse(Hier& H) {
             }
     const int nf = (int)free_idx.size();
     const int nb = nf + (H.nullspace ? 1 : 0);
+    if (nb > COARSE_MAX_DOFS) {
+        set_error("coarsest grid has " + std::to_string(nb) + " unknowns; the dense direct coarse solve "
+                  "takes at most " + std::to_string(COARSE_MAX_DOFS) + " (use a smaller n_coarse)");
+        throw Fail{SDX_EINVAL};
+    }
     std::vector<double> M((size_t)nb * nb, 0.0);
     std::vector<double> xh(4 * nn), yh(4 * nn);
     double* xd = L.x;
@@ -686,6 +691,32 @@ int sdx_smooth_pass(sdx_hier_t h, int level, int which, int colour, const double
     API_BEGIN
     launch_smooth_pass<double>(*H, level, which, colour, x, b, (cudaStream_t)stream);
     return launched("sdx_smooth_pass");
+    API_END
+}
+
+int sdx_apply_f32(sdx_hier_t h, int level, const float* x, float* y, void* stream) {
+    Hier* H = as_hier(h);
+    int c = check_level(H, level);
+    if (c) return c;
+    if (!x || !y) { set_error("null vector"); return SDX_EINVAL; }
+    if (H->prec != SDX_PREC_FP32_REFINED) { set_error("hierarchy was not created for FP32"); return SDX_EINVAL; }
+    API_BEGIN
+    launch_apply<float>(*H, level, x, y, nullptr, (cudaStream_t)stream);
+    return launched("sdx_apply_f32");
+    API_END
+}
+
+int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const float* b, float* x,
+                        void* stream) {
+    Hier* H = as_hier(h);
+    int c = check_level(H, level);
+    if (c) return c;
+    if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
+    if ((which != 0 && which != 1) || (colour != 0 && colour != 1)) { set_error("which and colour must be 0 or 1"); return SDX_EINVAL; }
+    if (H->prec != SDX_PREC_FP32_REFINED) { set_error("hierarchy was not created for FP32"); return SDX_EINVAL; }
+    API_BEGIN
+    launch_smooth_pass<float>(*H, level, which, colour, x, b, (cudaStream_t)stream);
+    return launched("sdx_smooth_pass_f32");
     API_END
 }
 

@@ -19,7 +19,8 @@ constexpr uint16_t INFO_SPECIAL = 8;   // not (interior node with 8 cells of one
 constexpr uint16_t INFO_IFACE = 16;    // interface row: decoupled form adds cross-couplings
 constexpr uint8_t CELL_OUTSIDE = 255;  // id of the ghost cells around the domain
 
-constexpr double OMEGA = 0.3;          // pressure Gauss-Seidel relaxation (Sec. 5)
+constexpr double OMEGA = 0.3;
+constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle matrix (1.2 GB)          // pressure Gauss-Seidel relaxation (Sec. 5)
 
 // Read-only view of one level as seen by kernels, for arithmetic type T.
 template <typename T>

@@ -27,7 +27,7 @@ OUTER_VCYCLE, OUTER_FGMRES = 0, 1
 
 EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_constraint_mask",
             "sdx_interface_mask", "sdx_apply", "sdx_residual", "sdx_rhs", "sdx_uzawa", "sdx_smooth_pass",
-            "sdx_kernel_launches",
+            "sdx_kernel_launches", "sdx_apply_f32", "sdx_smooth_pass_f32",
             "sdx_restrict", "sdx_prolong_add", "sdx_vcycle", "sdx_solve", "sdx_solve_host",
             "sdx_last_error", "sdx_strerror")
 
@@ -77,6 +77,8 @@ def load() -> ctypes.CDLL:
         "sdx_rhs": [P, P, P, P],
         "sdx_uzawa": [P, I, P, P, P],
         "sdx_smooth_pass": [P, I, I, I, P, P, P],
+        "sdx_apply_f32": [P, I, P, P, P],
+        "sdx_smooth_pass_f32": [P, I, I, I, P, P, P],
         "sdx_restrict": [P, I, P, P, P],
         "sdx_prolong_add": [P, I, P, P, P],
         "sdx_vcycle": [P, P, P, P],
@@ -103,13 +105,13 @@ def _check(code: int, allow=(OK,)) -> int:
     return code
 
 
-def _ptr(t) -> int:
+def _ptr(t, itemsize: int = 8) -> int:
     if t is None:
         return None
     if isinstance(t, int):
         return t
-    if t.dtype.itemsize != 8 or not t.is_contiguous() or not t.is_cuda:
-        raise ValueError("vectors must be contiguous float64 CUDA tensors")
+    if t.dtype.itemsize != itemsize or not t.is_contiguous() or not t.is_cuda:
+        raise ValueError(f"vectors must be contiguous {8 * itemsize}-bit float CUDA tensors")
     return t.data_ptr()
 
 
@@ -205,6 +207,12 @@ class Hierarchy:
 
     def sdx_smooth_pass(self, level, which, colour, b, x, stream=None):
         _check(load().sdx_smooth_pass(self._h, level, which, colour, _ptr(b), _ptr(x), _stream(stream)))
+
+    def sdx_apply_f32(self, level, x, y, stream=None):
+        _check(load().sdx_apply_f32(self._h, level, _ptr(x, 4), _ptr(y, 4), _stream(stream)))
+
+    def sdx_smooth_pass_f32(self, level, which, colour, b, x, stream=None):
+        _check(load().sdx_smooth_pass_f32(self._h, level, which, colour, _ptr(b, 4), _ptr(x, 4), _stream(stream)))
 
     def sdx_restrict(self, level, r_fine, b_coarse, stream=None):
         _check(load().sdx_restrict(self._h, level, _ptr(r_fine), _ptr(b_coarse), _stream(stream)))

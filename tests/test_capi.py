@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def _declared():
     text = open(os.path.join(ROOT, "include", "sdx.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sdx_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sdx_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_documented_entry_points():
@@ -75,3 +75,4 @@ def test_strerror_and_argument_validation_without_a_device():
     # null hierarchy handles
     assert lib.sdx_apply(None, 0, None, None, None) == sdx.EINVAL
     assert lib.sdx_destroy(None) == sdx.OK
+

@@ -130,7 +130,7 @@ def test_uzawa_step_matches_oracle(sdx, name, form):
 def test_transfers_match_oracle(sdx, name):
     p = PROBLEMS[name]
     OH = OracleHierarchy(p.n, p.n // 2, p.cell_mu().ravel(), p.face, "tr")
-    H = sdx.Hierarchy.from_problem(W.Problem(p.n, p.n // 2, p.cell_id, p.mu, p.face, p.forcing))
+    H = sdx.Hierarchy.from_problem(p)  # level 1 of the full hierarchy is the grid n/2
     fine, coarse = OH.levels
     rf = _masked_random(fine.disc, 9)
     bc = _dev(np.zeros(4 * coarse.nn))
@@ -234,3 +234,13 @@ def test_full_size_apply_sampled_rows(sdx):
     for form in ("tr",):
         ys = sampled_rows(p.n, cm, p.face, form, x, nodes)
         assert np.abs(ys - yh[:, nodes]).max() <= APPLY_TOL * np.abs(yh).max()
+
+
+def test_oversized_coarsest_grid_is_rejected(sdx):
+    """The dense coarse solve takes at most 12000 unknowns: a 24^3 coarsest grid is refused
+    with SDX_EINVAL instead of attempting a 60k x 60k inverse."""
+    p = W.Problem(n=24, n_coarse=24, cell_id=np.zeros((24, 24, 24), dtype=np.uint8), mu=np.array([1.0]),
+                  face=(0,) * 6, forcing=None)
+    with pytest.raises(sdx.SdxError) as e:
+        sdx.Hierarchy.from_problem(p)
+    assert e.value.code == sdx.EINVAL and "coarsest grid" in str(e.value)
