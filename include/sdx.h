@@ -150,6 +150,28 @@ int sdx_apply_f32(sdx_hier_t h, int level, const float* x, float* y, void* strea
 int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const float* b, float* x,
                         void* stream);
 
+/* Allocation-free variant of the velocity pass of sdx_smooth_pass (which = 0), FP64.
+ * The paper has no counterpart; this exists for callers that cannot allocate device memory at
+ * the point of the call - for example code running in a phase where cudaMalloc is forbidden
+ * because it would synchronise the device or because device memory is budgeted up front - and
+ * that do not want the pass to depend on a scratch buffer sized by the hierarchy.  It computes
+ * exactly what sdx_smooth_pass(h, level, 0, colour, b, x, stream) computes, but the new
+ * values of the boundary/interface rows are staged in a fixed array compiled into the
+ * library (SDX_NOALLOC_MAX_ROWS rows, 3 doubles each: 1.5 MiB that every GPU which loads the
+ * library holds until the process exits).  The call allocates nothing.
+ *   - Decoupled and gradient forms only: the strain form's pass needs a full-grid scratch
+ *     vector and is rejected with SDX_EINVAL.
+ *   - A level whose colour has more than SDX_NOALLOC_MAX_ROWS boundary/interface rows is
+ *     rejected with SDX_EINVAL before anything is launched (see sdx_last_error()).
+ *   - The first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - All calls share the one array.  Nothing in it needs to start at zero (each call writes
+ *     every entry it later reads), but calls whose executions overlap on the GPU (different
+ *     streams, different hierarchies) race on it: serialise them. */
+#define SDX_NOALLOC_MAX_ROWS 65536
+int sdx_smooth_pass_noalloc(sdx_hier_t h, int level, int colour, const double* b, double* x,
+                            void* stream);
+
 /* Transfers between level l (fine) and l+1 (coarse), standard nested P1 operators:
  * sdx_restrict writes b_coarse = P^T r_fine; sdx_prolong_add does x_fine += P e_coarse.
  * Constrained DoFs are masked on both levels.  FP64. */

@@ -2,6 +2,8 @@
 // side, vector helpers and the dense coarse-grid solve.
 #include <atomic>
 #include <cstdio>
+#include <mutex>
+#include <string>
 
 #include "sdx_internal.h"
 #include "stencil.cuh"
@@ -695,6 +697,70 @@ bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s) {
     cudaFree(col);
     cudaFree(status);
     return st == 0 && cudaGetLastError() == cudaSuccess;
+}
+
+// ------------------------------------------------------------------ allocation-free pass
+// Scratch of sdx_smooth_pass_noalloc: new velocity values of the special rows of one colour,
+// three doubles per row.  It lives in the library's module image, so every device that loads
+// the library holds these 1.5 MiB until the process exits; calls never allocate.
+static __device__ __align__(256) double g_noalloc_scratch[3 * NOALLOC_MAX_ROWS];
+
+// Device address of g_noalloc_scratch on the current device, looked up once per device.
+// (From host code the symbol name is only a host-side stand-in, never a device address.)
+static double* noalloc_scratch_address(std::string& err) {
+    static std::mutex mtx;
+    static void* addr[256] = {};
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 256) {
+        err = std::string("cudaGetDevice: ") + cudaGetErrorString(e);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lock(mtx);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p) {
+            err = std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e);
+            return nullptr;
+        }
+        addr[dev] = p;
+    }
+    return static_cast<double*>(addr[dev]);
+}
+
+template <int FORM>
+static void velocity_pass_static(const Hier& H, int l, int colour, double* x, const double* f,
+                                 double* tmp, cudaStream_t s) {
+    const Level& L = H.lv[l];
+    LevelView<double> V = view<double>(H, l);
+    dim3 grid(blocks_for((L.n + 2) / 2, 64), L.n + 1, L.n + 1);
+    const int cnt = L.n_spec_vel[colour];
+    count_launches(1 + (cnt ? 2 : 0));
+    if (cnt) k_vel_general<double, FORM><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, x, f, tmp);
+    k_vel_uniform<double, FORM><<<grid, 64, 0, s>>>(V, colour, x, f, nullptr);
+    if (cnt) k_vel_scatter<double><<<blocks_for(cnt), TPB, 0, s>>>(L.spec_vel[colour], cnt, tmp, x, L.nn);
+}
+
+int launch_velocity_pass_noalloc(const Hier& H, int l, int colour, double* x, const double* b,
+                                 cudaStream_t s, std::string& err) {
+    const Level& L = H.lv[l];
+    if (L.form == FORM_SYM) {
+        err = "sdx_smooth_pass_noalloc: the strain form's velocity pass needs a full-grid scratch "
+              "vector; use sdx_smooth_pass";
+        return -1;
+    }
+    if (L.n_spec_vel[colour] > NOALLOC_MAX_ROWS) {
+        err = "sdx_smooth_pass_noalloc: " + std::to_string(L.n_spec_vel[colour]) +
+              " boundary/interface rows in this colour exceed the fixed maximum of " +
+              std::to_string(NOALLOC_MAX_ROWS);
+        return -1;
+    }
+    double* tmp = noalloc_scratch_address(err);
+    if (!tmp) return -2;
+    if (L.form == FORM_GRAD) velocity_pass_static<FORM_GRAD>(H, l, colour, x, b, tmp, s);
+    else velocity_pass_static<FORM_TR>(H, l, colour, x, b, tmp, s);
+    return 0;
 }
 
 // explicit instantiations

@@ -720,6 +720,20 @@ int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const fl
     API_END
 }
 
+int sdx_smooth_pass_noalloc(sdx_hier_t h, int level, int colour, const double* b, double* x,
+                            void* stream) {
+    Hier* H = as_hier(h);
+    int c = check_level(H, level);
+    if (c) return c;
+    if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
+    if (colour != 0 && colour != 1) { set_error("colour must be 0 or 1"); return SDX_EINVAL; }
+    std::string err;
+    const int rc = launch_velocity_pass_noalloc(*H, level, colour, x, b, (cudaStream_t)stream, err);
+    if (rc == -1) { set_error(err); return SDX_EINVAL; }
+    if (rc == -2) { set_error(err); return SDX_ECUDA; }
+    return launched("sdx_smooth_pass_noalloc");
+}
+
 int sdx_restrict(sdx_hier_t h, int level, const double* rf, double* bc, void* stream) {
     Hier* H = as_hier(h);
     int c = check_level(H, level);

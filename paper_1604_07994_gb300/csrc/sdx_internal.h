@@ -128,6 +128,13 @@ void launch_coarse_solve(const Hier& H, const T* b, T* x, cudaStream_t s);
 // Gauss-Jordan inverse with partial pivoting on the device; returns false if singular
 bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s);
 
+// Allocation-free velocity colour pass (decoupled and gradient forms, FP64): the special-row
+// scratch is a static device array of NOALLOC_MAX_ROWS rows.  Returns 0, -1 (bad argument,
+// err set) or -2 (CUDA error, err set).
+constexpr int NOALLOC_MAX_ROWS = 65536;
+int launch_velocity_pass_noalloc(const Hier& H, int l, int colour, double* x, const double* b,
+                                 cudaStream_t s, std::string& err);
+
 // kernel-launch counter (add the number of launches issued)
 void count_launches(long long k);
 long long launches_total();

@@ -24,10 +24,11 @@ FORMS = {"tr": FORM_DECOUPLED, "decoupled": FORM_DECOUPLED, "sym": FORM_STRAIN,
          "strain": FORM_STRAIN, "grad": FORM_GRADIENT, "gradient": FORM_GRADIENT}
 PREC_FP64, PREC_FP32_REFINED = 0, 1
 OUTER_VCYCLE, OUTER_FGMRES = 0, 1
+NOALLOC_MAX_ROWS = 65536
 
 EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_constraint_mask",
             "sdx_interface_mask", "sdx_apply", "sdx_residual", "sdx_rhs", "sdx_uzawa", "sdx_smooth_pass",
-            "sdx_kernel_launches", "sdx_apply_f32", "sdx_smooth_pass_f32",
+            "sdx_kernel_launches", "sdx_smooth_pass_noalloc", "sdx_apply_f32", "sdx_smooth_pass_f32",
             "sdx_restrict", "sdx_prolong_add", "sdx_vcycle", "sdx_solve", "sdx_solve_host",
             "sdx_last_error", "sdx_strerror")
 
@@ -77,6 +78,7 @@ def load() -> ctypes.CDLL:
         "sdx_rhs": [P, P, P, P],
         "sdx_uzawa": [P, I, P, P, P],
         "sdx_smooth_pass": [P, I, I, I, P, P, P],
+        "sdx_smooth_pass_noalloc": [P, I, I, P, P, P],
         "sdx_apply_f32": [P, I, P, P, P],
         "sdx_smooth_pass_f32": [P, I, I, I, P, P, P],
         "sdx_restrict": [P, I, P, P, P],
@@ -213,6 +215,9 @@ class Hierarchy:
 
     def sdx_smooth_pass_f32(self, level, which, colour, b, x, stream=None):
         _check(load().sdx_smooth_pass_f32(self._h, level, which, colour, _ptr(b, 4), _ptr(x, 4), _stream(stream)))
+
+    def sdx_smooth_pass_noalloc(self, level, colour, b, x, stream=None):
+        _check(load().sdx_smooth_pass_noalloc(self._h, level, colour, _ptr(b), _ptr(x), _stream(stream)))
 
     def sdx_restrict(self, level, r_fine, b_coarse, stream=None):
         _check(load().sdx_restrict(self._h, level, _ptr(r_fine), _ptr(b_coarse), _stream(stream)))
