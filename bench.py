@@ -44,6 +44,9 @@ def parse():
                     help="sweep: only time the operator apply and smoother passes (profiling)")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="arithmetic of --mode sweep")
     ap.add_argument("--form", default="tr", choices=["tr", "sym", "grad"])
+    ap.add_argument("--maxit", type=int, default=500,
+                    help="iteration cap per solve (profiling runs use a small cap)")
+    ap.add_argument("--no-details", action="store_true", help="skip sweeps, e2e, variants, CPU leg")
     return ap.parse_args()
 
 
@@ -195,7 +198,8 @@ def main():
 
     def step(h, xv):
         xv.zero_()
-        return h.sdx_solve(b, xv, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=RESTART)
+        return h.sdx_solve(b, xv, rtol=1e-8, maxit=args.maxit, outer=sdx.OUTER_FGMRES, restart=RESTART,
+                           allow_noconv=args.maxit < 500)
 
     def barrier():
         if ws > 1:
@@ -205,6 +209,7 @@ def main():
     for _ in range(args.warmup):
         st = step(H, x)
     barrier()
+    print(json.dumps({"launches_before_timed_region": sdx.sdx_kernel_launches()}), file=sys.stderr, flush=True)
     clocks = ClockSampler(local)
     clocks.start()
     l0 = sdx.sdx_kernel_launches()
@@ -227,7 +232,7 @@ def main():
     final_res = st["res"] / st["bnorm"]
 
     extra = {}
-    if rank == 0:
+    if rank == 0 and not args.no_details:
         extra = measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W)
     if ws > 1:
         torch.distributed.barrier()
@@ -324,10 +329,12 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
                   "entry_point": "sdx_solve_host (host b and x0 in, host x out)"}
     if not args.no_variants:
         var = {}
-        for name, form, prec in (("strain_fp64", "sym", sdx.PREC_FP64),
-                                 ("decoupled_fp32_refined", "tr", sdx.PREC_FP32_REFINED),
-                                 ("strain_fp32_refined", "sym", sdx.PREC_FP32_REFINED)):
-            H2 = sdx.Hierarchy.from_problem(prob, form=form, prec=prec)
+        for name, form, prec, cform in (("strain_fp64", "sym", sdx.PREC_FP64, None),
+                                        ("decoupled_fp32_refined", "tr", sdx.PREC_FP32_REFINED, None),
+                                        ("strain_fp32_refined", "sym", sdx.PREC_FP32_REFINED, None),
+                                        ("decoupled_symcoarse_fp64", "tr", sdx.PREC_FP64, "sym"),
+                                        ("decoupled_symcoarse_fp32_refined", "tr", sdx.PREC_FP32_REFINED, "sym")):
+            H2 = sdx.Hierarchy.from_problem(prob, form=form, prec=prec, coarse_form=cform)
             x2 = torch.zeros_like(b)
             st = H2.sdx_solve(b, x2, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)
             reps2 = 2

@@ -13,6 +13,7 @@ namespace sdx {
 namespace {
 
 constexpr int TPB = 256;
+constexpr int CTPB = 128;  // threads per block of the colour-pass kernels
 
 inline unsigned blocks_for(long long count, int tpb = TPB) {
     return (unsigned)((count + tpb - 1) / tpb);
@@ -25,14 +26,11 @@ __device__ __forceinline__ void node_ijk(long long b, int n1, int& i, int& j, in
     k = (int)(t / n1);
 }
 
+// Viscosity id of a uniform node: any of its eight cells, here the one with origin
+// (i-1, j-1, k-1), which sits at padded index (i, j, k).
 template <typename T>
-__device__ __forceinline__ T uniform_mu(const LevelView<T>& L, int i, int j, int k) {
-    // any of the eight cells: take the one with origin (i-1, j-1, k-1)
-    return L.mu[L.cid[i + (long long)L.P * (j + (long long)L.P * k)]];
-}
-template <typename T>
-__device__ __forceinline__ T uniform_tau(const LevelView<T>& L, int i, int j, int k) {
-    return L.tau[L.cid[i + (long long)L.P * (j + (long long)L.P * k)]];
+__device__ __forceinline__ int uniform_id(const LevelView<T>& L, int i, int j, int k) {
+    return L.cid[i + (long long)L.P * (j + (long long)L.P * k)];
 }
 
 // ------------------------------------------------------------------ apply / residual
@@ -45,9 +43,10 @@ __global__ void k_apply_uniform(LevelView<T> L, const T* __restrict__ x, T* __re
     if (L.info[node] & INFO_SPECIAL) return;
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
-    const T mu = uniform_mu(L, i, j, k);
-    const T tau = uniform_tau(L, i, j, k);
-    const T h = L.h, h2 = L.h * L.h;
+    const int id = uniform_id(L, i, j, k);
+    const T muh = L.muh[id];
+    const T tauh = L.tauh[id];
+    const T h2 = L.h * L.h;
     const long long nn = L.nn;
     Nb15<T> P;
     load_nb15(x + 3 * nn, node, L, P);
@@ -67,10 +66,10 @@ __global__ void k_apply_uniform(LevelView<T> L, const T* __restrict__ x, T* __re
             for (int ii = 0; ii < 3; ++ii)
                 if (ii != jj) lap += xstencil(U[ii], ii, jj);
         }
-        const T row = mu * h * lap - h2 * bstencil(P, jj);
+        const T row = muh * lap - h2 * bstencil(P, jj);
         y[jj * nn + node] = b ? b[jj * nn + node] - row : row;
     }
-    const T cp = tau * h * (T(6) * P.c - (P.S(EX) + P.S(EY) + P.S(EZ)));
+    const T cp = tauh * (T(6) * P.c - (P.S(EX) + P.S(EY) + P.S(EZ)));
     const T rowp = h2 * bu - cp;
     y[3 * nn + node] = b ? b[3 * nn + node] - rowp : rowp;
 }
@@ -85,9 +84,17 @@ __global__ void k_apply_general(LevelView<T> L, const int* __restrict__ list, in
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
     const uint16_t inf = L.info[node];
+    const long long nn = L.nn;
+    if ((inf & 7) == 7) {  // all velocity components fixed: only the pressure row remains
+        T bu, cp, dC;
+        general_prow<T>(L, x, i, j, k, bu, cp, dC);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y[c * nn + node] = T(0);
+        y[3 * nn + node] = b ? b[3 * nn + node] - (bu - cp) : bu - cp;
+        return;
+    }
     GenRow<T> R;
     general_row<T, FORM>(L, x, i, j, k, (inf & INFO_IFACE) != 0, R);
-    const long long nn = L.nn;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         T row = R.au[c] + R.btp[c];
@@ -105,14 +112,18 @@ struct ColourIdx {
     int i, j, k;
     bool valid;
 };
+// Dense mapping of a 1-D grid onto the nodes of one colour: rows (j, k) of half = (n1+1)/2
+// slots, slot t of a row is node i = 2t + ((colour + j + k) & 1).
 __device__ __forceinline__ ColourIdx colour_node(int n1, int colour) {
     ColourIdx c;
-    c.j = blockIdx.y;
-    c.k = blockIdx.z;
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    int i0 = (colour + c.j + c.k) & 1;
-    c.i = 2 * t + i0;
-    c.valid = c.i < n1;
+    const int half = (n1 + 1) >> 1;
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long row = t / half;
+    const int slot = (int)(t - row * half);
+    c.j = (int)(row % n1);
+    c.k = (int)(row / n1);
+    c.i = 2 * slot + ((colour + c.j + c.k) & 1);
+    c.valid = c.k < n1 && c.i < n1;
     return c;
 }
 
@@ -126,8 +137,10 @@ __global__ void k_vel_uniform(LevelView<T> L, int colour, T* __restrict__ x,
     if (!ci.valid) return;
     const long long node = ci.i + L.s1 * ci.j + L.s2 * ci.k;
     if (L.info[node] & INFO_SPECIAL) return;
-    const T mu = uniform_mu(L, ci.i, ci.j, ci.k);
-    const T h = L.h, h2 = L.h * L.h;
+    const int id = uniform_id(L, ci.i, ci.j, ci.k);
+    const T muh = L.muh[id];
+    const T inv = L.idA[id];
+    const T h2 = L.h * L.h;
     const long long nn = L.nn;
     Nb15<T> P;
     load_nb15(x + 3 * nn, node, L, P);
@@ -135,23 +148,21 @@ __global__ void k_vel_uniform(LevelView<T> L, int colour, T* __restrict__ x,
         Nb15<T> U[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) load_nb15(x + c * nn, node, L, U[c]);
-        const T inv = T(1) / (T(8) * mu * h);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             T lap = T(8) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj);
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
                 if (ii != jj) lap += xstencil(U[ii], ii, jj);
-            const T row = mu * h * lap - h2 * bstencil(P, jj);
+            const T row = muh * lap - h2 * bstencil(P, jj);
             out[jj * nn + node] = U[jj].c + (f[jj * nn + node] - row) * inv;
         }
     } else {
-        const T inv = T(1) / (T(6) * mu * h);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             T* u = x + jj * nn;
             const T c = u[node];
-            const T row = mu * h * lap7(u, node, L, c) - h2 * bstencil(P, jj);
+            const T row = muh * lap7(u, node, L, c) - h2 * bstencil(P, jj);
             u[node] = c + (f[jj * nn + node] - row) * inv;
         }
     }
@@ -213,8 +224,8 @@ __global__ void k_pre_uniform(LevelView<T> L, int colour, T* __restrict__ x,
     if (!ci.valid) return;
     const long long node = ci.i + L.s1 * ci.j + L.s2 * ci.k;
     if (L.info[node] & INFO_SPECIAL) return;
-    const T tau = uniform_tau(L, ci.i, ci.j, ci.k);
-    const T h = L.h, h2 = L.h * L.h;
+    const int id = uniform_id(L, ci.i, ci.j, ci.k);
+    const T h2 = L.h * L.h;
     const long long nn = L.nn;
     T bu = 0;
 #pragma unroll
@@ -225,9 +236,9 @@ __global__ void k_pre_uniform(LevelView<T> L, int colour, T* __restrict__ x,
     }
     T* p = x + 3 * nn;
     const T pc = p[node];
-    const T cp = tau * h * lap7(p, node, L, pc);
+    const T cp = L.tauh[id] * lap7(p, node, L, pc);
     const T s = h2 * bu - cp - g[node];
-    p[node] = pc + T(OMEGA) * s / (T(6) * tau * h);
+    p[node] = pc + s * L.idC[id];
 }
 
 template <typename T, int FORM>
@@ -238,12 +249,207 @@ __global__ void k_pre_general(LevelView<T> L, const int* __restrict__ list, int 
     const long long node = list[t];
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
-    GenRow<T> R;
-    // the velocity part is not needed; FORM_GRAD skips all cross terms
-    general_row<T, FORM_GRAD>(L, x, i, j, k, false, R);
+    T bu, cp, dC;
+    general_prow<T>(L, x, i, j, k, bu, cp, dC);
     T* p = x + 3 * L.nn;
-    const T s = R.bu - R.cp - g[node];
-    p[node] = p[node] + T(OMEGA) * s / R.dC;
+    const T s = bu - cp - g[node];
+    p[node] = p[node] + T(OMEGA) * s / dC;
+}
+
+// ------------------------------------------------------------------ special rows, 8 groups each
+// A block of 256 threads serves 32 consecutive rows of the list: warp w (0..7) evaluates the
+// tetrahedra w, w+8, w+16 of every row (lanes = rows, so loads stay coalesced along the list),
+// the 8 partial rows are summed in shared memory by warp 0, which writes the result.
+constexpr int SPEC_ROWS = 32;
+
+template <typename T>
+struct SpecPart {
+    T v[12][8][SPEC_ROWS];
+};
+
+template <typename T>
+__device__ __forceinline__ void spec_store(SpecPart<T>& sp, int w, int r, const GenRow<T>& R) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        sp.v[j][w][r] = R.au[j];
+        sp.v[3 + j][w][r] = R.dA[j];
+        sp.v[6 + j][w][r] = R.btp[j];
+    }
+    sp.v[9][w][r] = R.bu;
+    sp.v[10][w][r] = R.cp;
+    sp.v[11][w][r] = R.dC;
+}
+
+template <typename T>
+__device__ __forceinline__ void spec_sum(const SpecPart<T>& sp, int r, GenRow<T>& R) {
+    T acc[12];
+#pragma unroll
+    for (int f = 0; f < 12; ++f) {
+        T a = sp.v[f][0][r];
+#pragma unroll
+        for (int w = 1; w < 8; ++w) a += sp.v[f][w][r];
+        acc[f] = a;
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { R.au[j] = acc[j]; R.dA[j] = acc[3 + j]; R.btp[j] = acc[6 + j]; }
+    R.bu = acc[9]; R.cp = acc[10]; R.dC = acc[11];
+}
+
+template <typename T, int FORM, int MODE>  // MODE 0: apply/residual, 1: velocity update, 2: pressure update
+__global__ void __launch_bounds__(256) k_special(LevelView<T> L, const int* __restrict__ list, int count,
+                                                 T* __restrict__ x, T* __restrict__ y,
+                                                 const T* __restrict__ b) {
+    __shared__ SpecPart<T> sp;
+    const int r = threadIdx.x & (SPEC_ROWS - 1);
+    const int w = threadIdx.x >> 5;
+    const int slot = blockIdx.x * SPEC_ROWS + r;
+    const bool valid = slot < count;
+    GenRow<T> R;
+    genrow_zero(R);
+    long long node = 0;
+    uint16_t inf = 7;
+    if (valid) {
+        node = list[slot];
+        inf = L.info[node];
+        int i, j, k;
+        node_ijk(node, L.n1, i, j, k);
+        const bool cross = (inf & INFO_IFACE) != 0;
+        const ArrayAcc<T> X{x, L.nn};
+        if (MODE == 2 || (inf & 7) == 7) {
+            for (int q = 0; q < 3; ++q) tet_row<T, FORM, true>(L, X, i, j, k, w + 8 * q, cross, R);
+        } else {
+            for (int q = 0; q < 3; ++q) tet_row<T, FORM, false>(L, X, i, j, k, w + 8 * q, cross, R);
+        }
+    }
+    spec_store(sp, w, r, R);
+    __syncthreads();
+    if (w != 0 || !valid) return;
+    spec_sum(sp, r, R);
+    const long long nn = L.nn;
+    if (MODE == 0) {  // y = K x, or y = b - K x
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T row = R.au[c] + R.btp[c];
+            T out = b ? b[c * nn + node] - row : row;
+            if (inf & (1u << c)) out = T(0);
+            y[c * nn + node] = out;
+        }
+        const T rowp = R.bu - R.cp;
+        y[3 * nn + node] = b ? b[3 * nn + node] - rowp : rowp;
+    } else if (MODE == 1) {  // new velocity values into y = tmp[3 * slot + c]
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            T v = T(0);
+            if (!(inf & (1u << c)))
+                v = x[c * nn + node] + (b[c * nn + node] - (R.au[c] + R.btp[c])) / R.dA[c];
+            y[3 * (long long)slot + c] = v;
+        }
+    } else {  // pressure Gauss-Seidel in place, b = g
+        T* p = x + 3 * nn;
+        const T s = R.bu - R.cp - b[node];
+        p[node] = p[node] + T(OMEGA) * s / R.dC;
+    }
+}
+
+// ------------------------------------------------------------------ special rows as stencils
+// The 15 Kuhn offsets of a node's stencil: 0, then +-e_x, +-e_y, +-e_z, +-(1,1,0), +-(1,0,1),
+// +-(0,1,1), +-(1,1,1).
+__device__ __constant__ signed char KOFF15[15][3] = {
+    {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}, {1, 1, 0},
+    {-1, -1, 0}, {1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, -1, -1}, {1, 1, 1}, {-1, -1, -1}};
+
+// Coefficients of special rows by evaluating the element-wise row on unit vectors: thread
+// (slot, col) with col = c * 15 + d applies the row of node list[slot] to the unit vector at
+// (component c, node + offset d).  rows: first row component stored (0 velocity / 3 pressure),
+// nrow: number of row components stored; diag: append diag(A) rows or diag(C).
+template <int FORM>
+__global__ void k_build_coef(LevelView<double> L, const int* __restrict__ list, int count, int r0,
+                             int nrow, bool diag, double* __restrict__ out) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= 60LL * count) return;
+    const int slot = (int)(t / 60), col = (int)(t % 60);
+    const int c = col / 15, d = col % 15;
+    const long long node = list[slot];
+    int i, j, k;
+    node_ijk(node, L.n1, i, j, k);
+    const int a = i + KOFF15[d][0], bb = j + KOFF15[d][1], cc = k + KOFF15[d][2];
+    const bool inside = a >= 0 && bb >= 0 && cc >= 0 && a < L.n1 && bb < L.n1 && cc < L.n1;
+    const uint16_t inf = L.info[node];
+    GenRow<double> R;
+    genrow_zero(R);
+    const UnitAcc<double> X{c, inside ? a + L.s1 * bb + L.s2 * cc : -1};
+    for (int q = 0; q < 24; ++q) tet_row<double, FORM, false>(L, X, i, j, k, q, (inf & INFO_IFACE) != 0, R);
+    for (int r = 0; r < nrow; ++r) {
+        const int rc = r0 + r;
+        const double v = rc < 3 ? R.au[rc] + R.btp[rc] : R.bu - R.cp;
+        out[(long long)(r * 60 + col) * count + slot] = v;
+    }
+    if (diag && col == 0) {
+        if (r0 == 0)
+            for (int r = 0; r < 3; ++r) out[(long long)(180 + r) * count + slot] = R.dA[r];
+        else
+            out[(long long)60 * count + slot] = R.dC;
+    }
+}
+
+__global__ void k_d2f_plain(float* y, const double* x, long long count) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) y[t] = (float)x[t];
+}
+
+// Special rows from their stored coefficients.  MODE 0: y = K x (or b - K x) on full rows;
+// MODE 3: the same on pressure-only rows (velocity rows written as 0); MODE 1: new velocity
+// values of a colour into tmp[3 * slot + r]; MODE 2: pressure Gauss-Seidel in place (b = g).
+template <typename T, int MODE>
+__global__ void k_spec_rows(LevelView<T> L, const int* __restrict__ list, int count,
+                            const T* __restrict__ cf, T* __restrict__ x, T* __restrict__ y,
+                            const T* __restrict__ b) {
+    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
+    if (slot >= count) return;
+    const long long node = list[slot];
+    int i, j, k;
+    node_ijk(node, L.n1, i, j, k);
+    const uint16_t inf = L.info[node];
+    const long long nn = L.nn;
+    constexpr int NR = MODE == 0 ? 4 : (MODE == 1 ? 3 : 1);  // row components stored
+    T acc[NR];
+#pragma unroll
+    for (int r = 0; r < NR; ++r) acc[r] = T(0);
+#pragma unroll
+    for (int d = 0; d < 15; ++d) {
+        const int a = i + KOFF15[d][0], bb = j + KOFF15[d][1], cc = k + KOFF15[d][2];
+        if (a < 0 || bb < 0 || cc < 0 || a >= L.n1 || bb >= L.n1 || cc >= L.n1) continue;
+        const long long v = a + L.s1 * bb + L.s2 * cc;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const T xv = x[c * nn + v];
+#pragma unroll
+            for (int r = 0; r < NR; ++r) acc[r] += cf[(long long)(r * 60 + c * 15 + d) * count + slot] * xv;
+        }
+    }
+    if (MODE == 0) {
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            T out = b ? b[r * nn + node] - acc[r] : acc[r];
+            if (r < 3 && (inf & (1u << r))) out = T(0);
+            y[r * nn + node] = out;
+        }
+    } else if (MODE == 3) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) y[r * nn + node] = T(0);
+        y[3 * nn + node] = b ? b[3 * nn + node] - acc[0] : acc[0];
+    } else if (MODE == 1) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            T v = T(0);
+            if (!(inf & (1u << r)))
+                v = x[r * nn + node] + (b[r * nn + node] - acc[r]) / cf[(long long)(180 + r) * count + slot];
+            y[3 * (long long)slot + r] = v;
+        }
+    } else {
+        T* p = x + 3 * nn;
+        p[node] = p[node] + T(OMEGA) * (acc[0] - b[node]) / cf[(long long)60 * count + slot];
+    }
 }
 
 // ------------------------------------------------------------------ transfers
@@ -385,6 +591,12 @@ __global__ void k_f2d_add(double* y, const float* x, const double* s, long long 
     if (t < count) y[t] += (double)x[t] * (s ? *s : 1.0);
 }
 
+// y = double(x) * s
+__global__ void k_f2d(double* y, const float* x, const double* s, long long count) {
+    long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < count) y[t] = (double)x[t] * (s ? *s : 1.0);
+}
+
 constexpr int RED_TPB = 512;
 __global__ void k_dot_part(const double* __restrict__ x, const double* __restrict__ y, long long count,
                            double* __restrict__ part) {
@@ -508,28 +720,50 @@ __global__ void k_gj_init(double* aug, const double* a, int n) {
 }  // namespace
 
 // ===================================================================== launchers
+static unsigned colour_blocks(const Level& L) {
+    const long long slots = (long long)((L.n + 2) / 2) * (L.n + 1) * (L.n + 1);
+    return (unsigned)((slots + CTPB - 1) / CTPB);
+}
+
 static std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 template <typename T>
+static const T* cf_full(const Level& L);
+template <> const double* cf_full<double>(const Level& L) { return L.cf_full_d; }
+template <> const float* cf_full<float>(const Level& L) { return L.cf_full_f; }
+template <typename T>
+static const T* cf_prow(const Level& L);
+template <> const double* cf_prow<double>(const Level& L) { return L.cf_prow_d; }
+template <> const float* cf_prow<float>(const Level& L) { return L.cf_prow_f; }
+template <typename T>
+static const T* cf_vel(const Level& L, int c);
+template <> const double* cf_vel<double>(const Level& L, int c) { return L.cf_vel_d[c]; }
+template <> const float* cf_vel<float>(const Level& L, int c) { return L.cf_vel_f[c]; }
+template <typename T>
+static const T* cf_pre(const Level& L, int c);
+template <> const double* cf_pre<double>(const Level& L, int c) { return L.cf_pre_d[c]; }
+template <> const float* cf_pre<float>(const Level& L, int c) { return L.cf_pre_f[c]; }
+
+template <typename T>
 static void apply_form(const Hier& H, int l, const T* x, T* y, const T* b, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
-    const unsigned gb = blocks_for(L.n_spec_all);
-    count_launches(1 + (L.n_spec_all ? 1 : 0));
+    count_launches(1 + (L.n_spec_full ? 1 : 0) + (L.n_spec_prow ? 1 : 0));
+    if (L.n_spec_full)
+        k_spec_rows<T, 0><<<blocks_for(L.n_spec_full), TPB, 0, s>>>(V, L.spec_full, L.n_spec_full, cf_full<T>(L), const_cast<T*>(x), y, b);
+    if (L.n_spec_prow)
+        k_spec_rows<T, 3><<<blocks_for(L.n_spec_prow), TPB, 0, s>>>(V, L.spec_prow, L.n_spec_prow, cf_prow<T>(L), const_cast<T*>(x), y, b);
     switch (L.form) {
         case FORM_SYM:
             k_apply_uniform<T, FORM_SYM><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
-            if (L.n_spec_all) k_apply_general<T, FORM_SYM><<<gb, TPB, 0, s>>>(V, L.spec_all, L.n_spec_all, x, y, b);
             break;
         case FORM_GRAD:
             k_apply_uniform<T, FORM_GRAD><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
-            if (L.n_spec_all) k_apply_general<T, FORM_GRAD><<<gb, TPB, 0, s>>>(V, L.spec_all, L.n_spec_all, x, y, b);
             break;
         default:
             k_apply_uniform<T, FORM_TR><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
-            if (L.n_spec_all) k_apply_general<T, FORM_TR><<<gb, TPB, 0, s>>>(V, L.spec_all, L.n_spec_all, x, y, b);
     }
 }
 
@@ -537,6 +771,37 @@ template <typename T>
 void launch_apply(const Hier& H, int l, const T* x, T* y, const T* b, cudaStream_t s) {
     apply_form<T>(H, l, x, y, b, s);
 }
+
+template <int FORM>
+static void build_coefs_form(const Hier& H, int l, cudaStream_t s) {
+    const Level& L = H.lv[l];
+    LevelView<double> V = view<double>(H, l);
+    auto run = [&](const int* list, int count, int r0, int nrow, bool diag, double* out, float* out_f, int ncoef) {
+        if (!count) return;
+        count_launches(1);
+        k_build_coef<FORM><<<blocks_for(60LL * count), TPB, 0, s>>>(V, list, count, r0, nrow, diag, out);
+        if (out_f) {
+            count_launches(1);
+            k_d2f_plain<<<blocks_for((long long)ncoef * count), TPB, 0, s>>>(out_f, out, (long long)ncoef * count);
+        }
+    };
+    run(L.spec_full, L.n_spec_full, 0, 4, false, L.cf_full_d, L.cf_full_f, 240);
+    run(L.spec_prow, L.n_spec_prow, 3, 1, false, L.cf_prow_d, L.cf_prow_f, 60);
+    for (int c = 0; c < 2; ++c) {
+        run(L.spec_vel[c], L.n_spec_vel[c], 0, 3, true, L.cf_vel_d[c], L.cf_vel_f[c], 183);
+        run(L.spec_pre[c], L.n_spec_pre[c], 3, 1, true, L.cf_pre_d[c], L.cf_pre_f[c], 61);
+    }
+}
+
+void build_special_coefs(const Hier& H, int l, cudaStream_t s) {
+    switch (H.lv[l].form) {
+        case FORM_SYM: build_coefs_form<FORM_SYM>(H, l, s); break;
+        case FORM_GRAD: build_coefs_form<FORM_GRAD>(H, l, s); break;
+        default: build_coefs_form<FORM_TR>(H, l, s);
+    }
+}
+
+
 
 template <typename T>
 static T* sym_scratch(const Level& L);
@@ -555,17 +820,17 @@ template <typename T, int FORM>
 static void velocity_pass(const Hier& H, int l, int colour, T* x, const T* f, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
-    dim3 grid(blocks_for((L.n + 2) / 2, 64), L.n + 1, L.n + 1);
+    const unsigned grid = colour_blocks(L);
     const int cnt = L.n_spec_vel[colour];
     T* tmp = spec_scratch<T>(L);
     count_launches((FORM == FORM_SYM ? 2 : 1) + (cnt ? 2 : 0));
-    if (cnt) k_vel_general<T, FORM><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, x, f, tmp);
+    if (cnt) k_spec_rows<T, 1><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, cf_vel<T>(L, colour), x, tmp, f);
     if (FORM == FORM_SYM) {
         T* out = sym_scratch<T>(L);
-        k_vel_uniform<T, FORM><<<grid, 64, 0, s>>>(V, colour, x, f, out);
-        k_vel_copy_colour<T><<<grid, 64, 0, s>>>(V, colour, out, x);
+        k_vel_uniform<T, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, out);
+        k_vel_copy_colour<T><<<grid, CTPB, 0, s>>>(V, colour, out, x);
     } else {
-        k_vel_uniform<T, FORM><<<grid, 64, 0, s>>>(V, colour, x, f, nullptr);
+        k_vel_uniform<T, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, nullptr);
     }
     if (cnt) k_vel_scatter<T><<<blocks_for(cnt), TPB, 0, s>>>(L.spec_vel[colour], cnt, tmp, x, L.nn);
 }
@@ -574,11 +839,11 @@ template <typename T>
 static void pressure_pass(const Hier& H, int l, int colour, T* x, const T* g, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
-    dim3 grid(blocks_for((L.n + 2) / 2, 64), L.n + 1, L.n + 1);
+    const unsigned grid = colour_blocks(L);
     const int cnt = L.n_spec_pre[colour];
     count_launches(1 + (cnt ? 1 : 0));
-    if (cnt) k_pre_general<T, FORM_GRAD><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_pre[colour], cnt, x, g);
-    k_pre_uniform<T><<<grid, 64, 0, s>>>(V, colour, x, g);
+    if (cnt) k_spec_rows<T, 2><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_pre[colour], cnt, cf_pre<T>(L, colour), x, nullptr, g);
+    k_pre_uniform<T><<<grid, CTPB, 0, s>>>(V, colour, x, g);
 }
 
 template <typename T>
@@ -656,6 +921,10 @@ void vec_f2d_add(double* y, const float* x, const double* sc, long long count, c
     count_launches(1);
     k_f2d_add<<<blocks_for(count), TPB, 0, s>>>(y, x, sc, count);
 }
+void vec_f2d(double* y, const float* x, const double* sc, long long count, cudaStream_t s) {
+    count_launches(1);
+    k_f2d<<<blocks_for(count), TPB, 0, s>>>(y, x, sc, count);
+}
 void vec_dot(const Hier& H, const double* x, const double* y, long long count, double* out, cudaStream_t s) {
     int blocks = (int)std::min<long long>(H.red_blocks, (count + RED_TPB - 1) / RED_TPB);
     if (blocks < 1) blocks = 1;
@@ -682,6 +951,7 @@ bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s) {
     if (cudaMalloc(&col, sizeof(double) * n) != cudaSuccess) { cudaFree(aug); return false; }
     if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) { cudaFree(aug); cudaFree(col); return false; }
     cudaMemsetAsync(status, 0, sizeof(int), s);
+    count_launches(2 + 3LL * n);
     k_gj_init<<<blocks_for((long long)n * 2 * n), TPB, 0, s>>>(aug, a_dev, n);
     dim3 eg(blocks_for(2 * n), n);
     for (int k = 0; k < n; ++k) {
@@ -734,11 +1004,11 @@ static void velocity_pass_static(const Hier& H, int l, int colour, double* x, co
                                  double* tmp, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<double> V = view<double>(H, l);
-    dim3 grid(blocks_for((L.n + 2) / 2, 64), L.n + 1, L.n + 1);
+    const unsigned grid = colour_blocks(L);
     const int cnt = L.n_spec_vel[colour];
     count_launches(1 + (cnt ? 2 : 0));
-    if (cnt) k_vel_general<double, FORM><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, x, f, tmp);
-    k_vel_uniform<double, FORM><<<grid, 64, 0, s>>>(V, colour, x, f, nullptr);
+    if (cnt) k_spec_rows<double, 1><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, L.cf_vel_d[colour], x, tmp, f);
+    k_vel_uniform<double, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, nullptr);
     if (cnt) k_vel_scatter<double><<<blocks_for(cnt), TPB, 0, s>>>(L.spec_vel[colour], cnt, tmp, x, L.nn);
 }
 

@@ -4,6 +4,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -47,6 +48,7 @@ LevelView<double> view<double>(const Hier& H, int l) {
     LevelView<double> v;
     v.n = L.n; v.n1 = L.n + 1; v.nn = L.nn; v.s1 = L.n + 1; v.s2 = (long long)(L.n + 1) * (L.n + 1);
     v.P = L.n + 2; v.h = L.h; v.cid = L.cid; v.info = L.info; v.mu = H.mu_d; v.tau = L.tau_d;
+    v.muh = L.tab_d; v.idA = L.tab_d + 256; v.tauh = L.tab_d + 512; v.idC = L.tab_d + 768;
     return v;
 }
 template <>
@@ -55,6 +57,7 @@ LevelView<float> view<float>(const Hier& H, int l) {
     LevelView<float> v;
     v.n = L.n; v.n1 = L.n + 1; v.nn = L.nn; v.s1 = L.n + 1; v.s2 = (long long)(L.n + 1) * (L.n + 1);
     v.P = L.n + 2; v.h = (float)L.h; v.cid = L.cid; v.info = L.info; v.mu = H.mu_f; v.tau = L.tau_f;
+    v.muh = L.tab_f; v.idA = L.tab_f + 256; v.tauh = L.tab_f + 512; v.idC = L.tab_f + 768;
     return v;
 }
 
@@ -106,7 +109,7 @@ static void build_level_host(const Hier& H, Level& L, const std::vector<uint8_t>
 
 static void upload_level(Hier& H, Level& L) {
     const int n1 = L.n + 1;
-    std::vector<int> all, vel[2], pre[2];
+    std::vector<int> all, full, prow, vel[2], pre[2];
     for (int k = 0; k < n1; ++k)
         for (int j = 0; j < n1; ++j)
             for (int i = 0; i < n1; ++i) {
@@ -116,7 +119,12 @@ static void upload_level(Hier& H, Level& L) {
                 const int c = (i + j + k) & 1;
                 all.push_back(node);
                 pre[c].push_back(node);
-                if ((inf & 7) != 7) vel[c].push_back(node);
+                if ((inf & 7) != 7) {
+                    vel[c].push_back(node);
+                    full.push_back(node);
+                } else {
+                    prow.push_back(node);
+                }
             }
     const size_t P3 = L.cid_host.size();
     L.cid = dalloc<uint8_t>((long long)P3);
@@ -129,6 +137,8 @@ static void upload_level(Hier& H, Level& L) {
         if (cnt) CK(cudaMemcpy(d, v.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice));
     };
     up(all, L.spec_all, L.n_spec_all);
+    up(full, L.spec_full, L.n_spec_full);
+    up(prow, L.spec_prow, L.n_spec_prow);
     for (int c = 0; c < 2; ++c) {
         up(vel[c], L.spec_vel[c], L.n_spec_vel[c]);
         up(pre[c], L.spec_pre[c], L.n_spec_pre[c]);
@@ -144,6 +154,23 @@ static void upload_level(Hier& H, Level& L) {
     L.tau_f = dalloc<float>(256);
     CK(cudaMemcpy(L.tau_d, tau.data(), sizeof(double) * 256, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.tau_f, tauf.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
+    // per-id constants of uniform nodes (diagonals are sums over the 24 tetrahedra around a node)
+    std::vector<double> tab(4 * 256, 0.0);
+    std::vector<float> tabf(4 * 256, 0.0f);
+    const double dA = L.form == FORM_SYM ? 8.0 : 6.0;
+    for (int id = 0; id < 255; ++id)
+        if (H.mu_table[id] > 0) {
+            const double muh = H.mu_table[id] * L.h, tauh = tau[id] * L.h;
+            tab[id] = muh;
+            tab[256 + id] = 1.0 / (dA * muh);
+            tab[512 + id] = tauh;
+            tab[768 + id] = OMEGA / (6.0 * tauh);
+        }
+    for (int i = 0; i < 4 * 256; ++i) tabf[i] = (float)tab[i];
+    L.tab_d = dalloc<double>(4 * 256);
+    L.tab_f = dalloc<float>(4 * 256);
+    CK(cudaMemcpy(L.tab_d, tab.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.tab_f, tabf.data(), sizeof(float) * 4 * 256, cudaMemcpyHostToDevice));
     const long long v4 = 4 * L.nn;
     L.x = dalloc<double>(v4);
     L.b = dalloc<double>(v4);
@@ -161,6 +188,21 @@ static void upload_level(Hier& H, Level& L) {
     const int mx = std::max(L.n_spec_vel[0], L.n_spec_vel[1]);
     L.spec_tmp = dalloc<double>(3LL * mx);
     if (H.prec == SDX_PREC_FP32_REFINED) L.spec_tmp32 = dalloc<float>(3LL * mx);
+    const bool f32 = H.prec == SDX_PREC_FP32_REFINED;
+    L.cf_full_d = dalloc<double>(240LL * L.n_spec_full);
+    L.cf_prow_d = dalloc<double>(60LL * L.n_spec_prow);
+    if (f32) {
+        L.cf_full_f = dalloc<float>(240LL * L.n_spec_full);
+        L.cf_prow_f = dalloc<float>(60LL * L.n_spec_prow);
+    }
+    for (int c = 0; c < 2; ++c) {
+        L.cf_vel_d[c] = dalloc<double>(183LL * L.n_spec_vel[c]);
+        L.cf_pre_d[c] = dalloc<double>(61LL * L.n_spec_pre[c]);
+        if (f32) {
+            L.cf_vel_f[c] = dalloc<float>(183LL * L.n_spec_vel[c]);
+            L.cf_pre_f[c] = dalloc<float>(61LL * L.n_spec_pre[c]);
+        }
+    }
 }
 
 // Coarsest-grid saddle matrix by probing with the device apply: the 27 node classes
@@ -270,14 +312,22 @@ static void free_hier(Hier* H) {
     if (!H) return;
     cudaDeviceSynchronize();
     for (Level& L : H->lv) {
-        void* ptrs[] = {L.cid, L.info, L.tau_d, L.tau_f, L.spec_all, L.spec_vel[0], L.spec_vel[1],
+        void* cfs[] = {L.spec_full, L.spec_prow, L.cf_full_d, L.cf_full_f, L.cf_prow_d, L.cf_prow_f,
+                       L.cf_vel_d[0], L.cf_vel_d[1], L.cf_vel_f[0], L.cf_vel_f[1],
+                       L.cf_pre_d[0], L.cf_pre_d[1], L.cf_pre_f[0], L.cf_pre_f[1]};
+        for (void* p : cfs)
+            if (p) cudaFree(p);
+        void* ptrs[] = {L.cid, L.info, L.tau_d, L.tau_f, L.tab_d, L.tab_f, L.spec_all, L.spec_vel[0], L.spec_vel[1],
                         L.spec_pre[0], L.spec_pre[1], L.x, L.b, L.r, L.x32, L.b32, L.r32,
                         L.sym_tmp, L.sym_tmp32, L.spec_tmp, L.spec_tmp32};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
     void* ptrs[] = {H->mu_d, H->mu_f, H->coarse.free_idx, H->coarse.kinv, H->coarse.bc,
-                    H->coarse.xc, H->red_part, H->scal, H->r0, H->xh, H->bh};
+                    H->coarse.xc, H->red_part, H->scal, H->r0, H->xh, H->bh, H->e};
+    if (H->g64.exec) cudaGraphExecDestroy(H->g64.exec);
+    if (H->g32.exec) cudaGraphExecDestroy(H->g32.exec);
+    if (H->cap) cudaStreamDestroy(H->cap);
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (H->scal_host) cudaFreeHost(H->scal_host);
@@ -353,6 +403,8 @@ static Hier* create(const sdx_desc* d) {
             ++lvl;
         }
         for (Level& L : H->lv) upload_level(*H, L);
+        for (int l = 0; l < (int)H->lv.size(); ++l) build_special_coefs(*H, l, 0);
+        CK(cudaGetLastError());
         H->red_blocks = 4 * 152;
         H->red_part = dalloc<double>(H->red_blocks);
         H->scal = dalloc<double>(256);
@@ -361,6 +413,9 @@ static Hier* create(const sdx_desc* d) {
         H->r0 = dalloc<double>(v4);
         H->xh = dalloc<double>(v4);
         H->bh = dalloc<double>(v4);
+        H->e = dalloc<double>(v4);
+        const char* ng = std::getenv("SDX_NO_GRAPH");
+        H->use_graph = !(ng && ng[0] == '1');
         build_coarse(*H);
         CK(cudaDeviceSynchronize());
     } catch (...) {
@@ -408,7 +463,7 @@ static void vcycle_rec(Hier& H, int l, T* x, const T* b, cudaStream_t s) {
 }
 
 // device scalar slots
-enum { S_DOT = 0, S_NORM = 1, S_H = 8 };
+enum { S_DOT = 0, S_NORM = 1, S_SCALE = 2, S_H = 8 };
 
 __global__ void k_sqrt(double* v) { *v = sqrt(*v); }
 
@@ -420,38 +475,75 @@ static double norm_sync(Hier& H, const double* v, cudaStream_t s) {
     return std::sqrt(H.scal_host[S_NORM]);
 }
 
-// z = M v : one V-cycle with zero initial guess (FP64 or FP32 inside)
-static void precondition(Hier& H, const double* v, double* z, cudaStream_t s) {
+// One V-cycle from zero on the finest level's own buffers: x0 = 0, then V_var(3,3) on
+// (x, b) of level 0 in arithmetic T.  Captured once into a CUDA graph and replayed.
+template <typename T>
+static void zero_start_cycle(Hier& H, cudaStream_t s) {
+    Level& L = H.lv[0];
+    vec_zero<T>(Buf<T>::x(L), 4 * L.nn, s);
+    vcycle_rec<T>(H, 0, Buf<T>::x(L), Buf<T>::b(L), s);
+}
+
+template <typename T>
+static void run_cycle(Hier& H, cudaStream_t s) {
+    CycleGraph& G = sizeof(T) == sizeof(double) ? H.g64 : H.g32;
+    if (!H.use_graph) {
+        zero_start_cycle<T>(H, s);
+        return;
+    }
+    if (!G.exec) {
+        if (!H.cap) CK(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
+        const long long before = launches_total();
+        CK(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
+        cudaGraph_t g = nullptr;
+        try {
+            zero_start_cycle<T>(H, H.cap);
+        } catch (...) {
+            cudaStreamEndCapture(H.cap, &g);
+            if (g) cudaGraphDestroy(g);
+            throw;
+        }
+        CK(cudaStreamEndCapture(H.cap, &g));
+        const cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
+        cudaGraphDestroy(g);
+        CK(e);
+        G.kernels = launches_total() - before;
+        count_launches(-G.kernels);  // captured, not executed
+    }
+    CK(cudaGraphLaunch(G.exec, s));
+    count_launches(G.kernels);
+}
+
+// z = M v : one V-cycle with zero initial guess applied to v (FP64 or FP32 inside).  With a
+// device scalar `scale`, the FP32 cycle runs on v / scale and the result is scaled back.
+static void precondition(Hier& H, const double* v, double* z, const double* scale, cudaStream_t s) {
     Level& L = H.lv[0];
     const long long v4 = 4 * L.nn;
-    vec_zero<double>(z, v4, s);
     if (H.prec == SDX_PREC_FP64) {
-        vcycle_rec<double>(H, 0, z, v, s);
+        vec_copy(L.b, v, v4, s);
+        run_cycle<double>(H, s);
+        vec_copy(z, L.x, v4, s);
     } else {
-        vec_d2f(L.b32, v, nullptr, v4, s);
-        vec_zero<float>(L.x32, v4, s);
-        vcycle_rec<float>(H, 0, L.x32, L.b32, s);
-        vec_f2d_add(z, L.x32, nullptr, v4, s);
+        vec_d2f(L.b32, v, scale, v4, s);
+        run_cycle<float>(H, s);
+        vec_f2d(z, L.x32, scale, v4, s);
     }
 }
 
-// one V-cycle in place on x for the hierarchy's precision
+// one V-cycle as a correction: r = b - K x, x += M r
 static void vcycle_inplace(Hier& H, const double* b, double* x, cudaStream_t s) {
     Level& L = H.lv[0];
     const long long v4 = 4 * L.nn;
-    if (H.prec == SDX_PREC_FP64) {
-        vcycle_rec<double>(H, 0, x, b, s);
-        return;
-    }
-    // r = b - K x in FP64, scaled to unit norm, cycled in FP32, added back in FP64
     launch_apply<double>(H, 0, x, H.r0, b, s);
-    vec_dot(H, H.r0, H.r0, v4, H.scal + S_NORM, s);
-    count_launches(1);
-    k_sqrt<<<1, 1, 0, s>>>(H.scal + S_NORM);
-    vec_d2f(L.b32, H.r0, H.scal + S_NORM, v4, s);
-    vec_zero<float>(L.x32, v4, s);
-    vcycle_rec<float>(H, 0, L.x32, L.b32, s);
-    vec_f2d_add(x, L.x32, H.scal + S_NORM, v4, s);
+    const double* scale = nullptr;
+    if (H.prec != SDX_PREC_FP64) {
+        vec_dot(H, H.r0, H.r0, v4, H.scal + S_NORM, s);
+        count_launches(1);
+        k_sqrt<<<1, 1, 0, s>>>(H.scal + S_NORM);
+        scale = H.scal + S_NORM;
+    }
+    precondition(H, H.r0, H.e, scale, s);
+    vec_axpy(x, H.e, 1.0, v4, s);
 }
 
 static void ensure_krylov(Hier& H, int m) {
@@ -482,9 +574,18 @@ static int solve(Hier& H, const double* b, double* x, double rtol, int maxit, in
     if (!std::isfinite(res) || !std::isfinite(S.bnorm)) return finish(SDX_ENONFINITE);
     const double tol = rtol * S.bnorm;
     if (outer == SDX_OUTER_VCYCLE) {
+        // defect correction: x += M (b - K x), the residual reused from the convergence test
         while (res > tol) {
             if (S.iterations >= maxit) return finish(SDX_ENOCONV);
-            vcycle_inplace(H, b, x, s);
+            const double* scale = nullptr;
+            if (H.prec != SDX_PREC_FP64) {
+                H.scal_host[S_SCALE] = res;
+                CK(cudaMemcpyAsync(H.scal + S_SCALE, H.scal_host + S_SCALE, sizeof(double),
+                                   cudaMemcpyHostToDevice, s));
+                scale = H.scal + S_SCALE;
+            }
+            precondition(H, H.r0, H.e, scale, s);
+            vec_axpy(x, H.e, 1.0, v4, s);
             S.iterations++;
             launch_apply<double>(H, 0, x, H.r0, b, s);
             res = norm_sync(H, H.r0, s);
@@ -509,7 +610,7 @@ static int solve(Hier& H, const double* b, double* x, double rtol, int maxit, in
         int j = 0, k = 0;
         bool done = false;
         for (j = 0; j < m; ++j) {
-            precondition(H, H.V[j], H.Z[j], s);
+            precondition(H, H.V[j], H.Z[j], nullptr, s);
             launch_apply<double>(H, 0, H.Z[j], H.V[j + 1], nullptr, s);
             for (int i = 0; i <= j; ++i) {
                 vec_dot(H, H.V[j + 1], H.V[i], v4, H.scal + S_H + i, s);

@@ -35,6 +35,10 @@ struct LevelView {
     const uint16_t* info;   // [nn]
     const T* mu;            // viscosity table [256], mu[CELL_OUTSIDE] = 0
     const T* tau;           // stabilisation weight beta h^2 / mu [256], 0 for outside
+    const T* muh;           // mu h [256]
+    const T* idA;           // 1 / diag(A) of a uniform node: 1/(6 mu h), strain form 1/(8 mu h)
+    const T* tauh;          // tau h [256]
+    const T* idC;           // omega / diag(C) of a uniform node: omega / (6 tau h)
 };
 
 // Device buffers of one level.
@@ -49,8 +53,18 @@ struct Level {
     uint16_t* info = nullptr;
     double* tau_d = nullptr;
     float* tau_f = nullptr;
+    double* tab_d = nullptr;   // [4][256]: mu h, 1/diag(A), tau h, omega/diag(C)
+    float* tab_f = nullptr;
     // special node lists (int32 node indices)
     int* spec_all = nullptr;  int n_spec_all = 0;
+    int* spec_full = nullptr; int n_spec_full = 0;   // special rows with a free velocity component
+    int* spec_prow = nullptr; int n_spec_prow = 0;   // special rows with all velocity fixed
+    // precomputed stencil coefficients of the special rows (SoA: [coefficient][row]);
+    // column (component c, Kuhn offset d) has index c * 15 + d, row component r adds r * 60
+    double* cf_full_d = nullptr; float* cf_full_f = nullptr;      // 240 per row
+    double* cf_prow_d = nullptr; float* cf_prow_f = nullptr;      // 60 per row (pressure row)
+    double* cf_vel_d[2] = {nullptr, nullptr}; float* cf_vel_f[2] = {nullptr, nullptr};  // 180 + 3 diag
+    double* cf_pre_d[2] = {nullptr, nullptr}; float* cf_pre_f[2] = {nullptr, nullptr};  // 60 + 1 diag
     int* spec_vel[2] = {nullptr, nullptr};  int n_spec_vel[2] = {0, 0};
     int* spec_pre[2] = {nullptr, nullptr};  int n_spec_pre[2] = {0, 0};
     long long free_dofs = 0;
@@ -67,6 +81,12 @@ struct Coarse {
     double* kinv = nullptr;     // [nf * nf] row-major inverse (top-left block if bordered)
     double* bc = nullptr;       // [nf]
     double* xc = nullptr;       // [nf]
+};
+
+// A captured zero-start V-cycle (CUDA graph) and the number of kernels one replay launches.
+struct CycleGraph {
+    cudaGraphExec_t exec = nullptr;
+    long long kernels = 0;
 };
 
 struct Hier {
@@ -88,6 +108,10 @@ struct Hier {
     double* r0 = nullptr;   double* xh = nullptr;  double* bh = nullptr;
     std::vector<double*> V, Z;
     int krylov_m = 0;
+    double* e = nullptr;            // correction of a V-cycle (finest level, FP64)
+    CycleGraph g64, g32;
+    cudaStream_t cap = nullptr;     // internal stream used only to capture the graphs
+    bool use_graph = true;
 };
 
 template <typename T>
@@ -106,6 +130,9 @@ template <typename T>
 void launch_prolong_add(const Hier& H, int l, const T* ec, T* xf, cudaStream_t s);
 void launch_rhs(const Hier& H, const double* f, double* b, cudaStream_t s);
 
+// Build the special-row coefficient arrays of level l (FP64, and FP32 copies if allocated).
+void build_special_coefs(const Hier& H, int l, cudaStream_t s);
+
 // vector helpers over count elements
 template <typename T>
 void vec_zero(T* v, long long count, cudaStream_t s);
@@ -118,6 +145,7 @@ void vec_copy(double* y, const double* x, long long count, cudaStream_t s);
 void vec_d2f(float* y, const double* x, const double* scal_dev, long long count, cudaStream_t s);
 void vec_f2d_add(double* y, const float* x, const double* scal_dev, long long count,
                  cudaStream_t s);
+void vec_f2d(double* y, const float* x, const double* scal_dev, long long count, cudaStream_t s);
 // dot(x, y) -> *out_dev (deterministic two-pass reduction)
 void vec_dot(const Hier& H, const double* x, const double* y, long long count, double* out_dev,
              cudaStream_t s);

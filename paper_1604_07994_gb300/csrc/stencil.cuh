@@ -206,4 +206,188 @@ __device__ void general_row(const LevelView<T>& L, const T* __restrict__ x, int 
     }
 }
 
+// Pressure row only (B u, C p and diag C) of node (bi, bj, bk), from its tetrahedra.
+template <typename T>
+__device__ void general_prow(const LevelView<T>& L, const T* __restrict__ x, int bi, int bj, int bk,
+                             T& bu, T& cp, T& dC) {
+    const T* ux = x;
+    const T* uy = x + L.nn;
+    const T* uz = x + 2 * L.nn;
+    const T* pp = x + 3 * L.nn;
+    bu = 0; cp = 0; dC = 0;
+    const T h = L.h;
+    const T wB = h * h / T(6);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+        const int ox = bi - qx, oy = bj - qy, oz = bk - qz;
+        const uint8_t id = L.cid[(ox + 1) + (long long)L.P * ((oy + 1) + (long long)L.P * (oz + 1))];
+        if (L.mu[id] == T(0)) continue;
+        const T wC = L.tau[id] * h / T(6);
+#pragma unroll
+        for (int s = 0; s < 6; ++s) {
+            int a0, a1, a2;
+            perm3(s, a0, a1, a2);
+            int qv[3] = {qx, qy, qz};
+            int m;
+            const int sum = qx + qy + qz;
+            if (sum == 0) m = 0;
+            else if (sum == 3) m = 3;
+            else if (sum == 1) { if (qv[a0] == 1) m = 1; else continue; }
+            else { if (qv[a2] == 0) m = 2; else continue; }
+            const long long st[3] = {1, L.s1, L.s2};
+            long long v[4];
+            v[0] = ox + L.s1 * oy + L.s2 * oz;
+            v[1] = v[0] + st[a0];
+            v[2] = v[1] + st[a1];
+            v[3] = v[2] + st[a2];
+            const T* uc[3] = {ux, uy, uz};
+            // h div u = sum over the path edges of the edge difference of the component along it
+            const T hdiv = (uc[a0][v[1]] - uc[a0][v[0]]) + (uc[a1][v[2]] - uc[a1][v[1]]) +
+                           (uc[a2][v[3]] - uc[a2][v[2]]);
+            T hP[3];
+            hP[a0] = pp[v[1]] - pp[v[0]];
+            hP[a1] = pp[v[2]] - pp[v[1]];
+            hP[a2] = pp[v[3]] - pp[v[2]];
+            T g[3] = {0, 0, 0};
+            if (m == 0) g[a0] = -1;
+            else if (m == 1) { g[a0] = 1; g[a1] = -1; }
+            else if (m == 2) { g[a1] = 1; g[a2] = -1; }
+            else g[a2] = 1;
+            bu -= T(0.25) * wB * hdiv;
+            cp += wC * (g[0] * hP[0] + g[1] * hP[1] + g[2] * hP[2]);
+            dC += wC * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ 8 lanes per row
+// The 24 tetrahedra around a node as (position q of the node in the cell, with the cell's
+// origin at node - (q&1, q>>1&1, q>>2&1); axis permutation s of the Kuhn path; index m of the
+// node on that path).  Lane l of a row's 8-lane group takes entries l, l+8 and l+16.
+__device__ __constant__ signed char TET24[24][3] = {
+    {0, 0, 0}, {0, 1, 0}, {0, 2, 0}, {0, 3, 0}, {0, 4, 0}, {0, 5, 0}, {1, 0, 1}, {1, 1, 1},
+    {2, 2, 1}, {2, 3, 1}, {3, 0, 2}, {3, 2, 2}, {4, 4, 1}, {4, 5, 1}, {5, 1, 2}, {5, 4, 2},
+    {6, 3, 2}, {6, 5, 2}, {7, 0, 3}, {7, 1, 3}, {7, 2, 3}, {7, 3, 3}, {7, 4, 3}, {7, 5, 3}};
+
+template <typename T>
+__device__ __forceinline__ T sel3(int i, T a, T b, T c) {
+    return i == 0 ? a : (i == 1 ? b : c);
+}
+
+// Contribution of tetrahedron `t` of TET24 to the row of node (bi, bj, bk), in path
+// coordinates: edge l (0..2) of the Kuhn path runs along axis a_l, D_l = u(v_{l+1}) - u(v_l)
+// is h times the derivative of u along that axis, and h grad lambda of the node has component
+// gl_l along a_l: (-1,0,0), (1,-1,0), (0,1,-1), (0,0,1) for path position m = 0..3.  Row j
+// of the velocity block uses the path edge l(j) along axis j.  PROW: pressure row only.
+// Vector accessors for tet_row: values of a SoA vector, or of one unit vector.
+template <typename T>
+struct ArrayAcc {
+    const T* x;
+    long long nn;
+    __device__ __forceinline__ T operator()(int c, long long node) const { return x[c * nn + node]; }
+};
+template <typename T>
+struct UnitAcc {
+    int c0;
+    long long node0;
+    __device__ __forceinline__ T operator()(int c, long long node) const {
+        return (c == c0 && node == node0) ? T(1) : T(0);
+    }
+};
+
+template <typename T, int FORM, bool PROW, class Acc>
+__device__ __forceinline__ void tet_row(const LevelView<T>& L, const Acc& X, int bi, int bj,
+                                        int bk, int t, bool cross, GenRow<T>& o) {
+    const int q = TET24[t][0], s = TET24[t][1], m = TET24[t][2];
+    const int ox = bi - (q & 1), oy = bj - ((q >> 1) & 1), oz = bk - ((q >> 2) & 1);
+    const uint8_t id = L.cid[(ox + 1) + (long long)L.P * ((oy + 1) + (long long)L.P * (oz + 1))];
+    const T mu = L.mu[id];
+    if (mu == T(0)) return;
+    const T h = L.h;
+    const T wA = mu * h / T(6);
+    const T wB = h * h / T(6);
+    const T wC = L.tau[id] * h / T(6);
+    int a0, a1, a2;
+    perm3(s, a0, a1, a2);
+    const long long s0 = a0 == 0 ? 1 : (a0 == 1 ? L.s1 : L.s2);
+    const long long s1 = a1 == 0 ? 1 : (a1 == 1 ? L.s1 : L.s2);
+    const long long s2 = a2 == 0 ? 1 : (a2 == 1 ? L.s1 : L.s2);
+    const long long v0 = ox + L.s1 * oy + L.s2 * oz, v1 = v0 + s0, v2 = v1 + s1, v3 = v2 + s2;
+    const T g0 = m == 0 ? T(-1) : (m == 1 ? T(1) : T(0));
+    const T g1 = m == 1 ? T(-1) : (m == 2 ? T(1) : T(0));
+    const T g2 = m == 2 ? T(-1) : (m == 3 ? T(1) : T(0));
+    const T gg = g0 * g0 + g1 * g1 + g2 * g2;
+    const T p0 = X(3, v0), p1 = X(3, v1), p2 = X(3, v2), p3 = X(3, v3);
+    o.cp += wC * (g0 * (p1 - p0) + g1 * (p2 - p1) + g2 * (p3 - p2));
+    o.dC += wC * gg;
+    // D_l[c] for the three path edges and three components
+    T D0[3], D1[3], D2[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const T u0 = X(c, v0), u1 = X(c, v1), u2 = X(c, v2), u3 = X(c, v3);
+        D0[c] = u1 - u0;
+        D1[c] = u2 - u1;
+        D2[c] = u3 - u2;
+    }
+    // component of D_l along the path edge's own axis, summed: h div u
+    const T hdiv = sel3(a0, D0[0], D0[1], D0[2]) + sel3(a1, D1[0], D1[1], D1[2]) +
+                   sel3(a2, D2[0], D2[1], D2[2]);
+    o.bu -= T(0.25) * wB * hdiv;
+    if (PROW) return;
+    const T pbar = T(0.25) * (p0 + p1 + p2 + p3);
+    // E_l = sum_l' gl_l' D_l[a_l'] = h^2 sum_i d_i lambda d_{a_l} u_i (strain cross term)
+    T E0 = 0, E1 = 0, E2 = 0;
+    if (FORM == FORM_SYM || (FORM == FORM_TR && cross)) {
+        E0 = g0 * sel3(a0, D0[0], D0[1], D0[2]) + g1 * sel3(a1, D0[0], D0[1], D0[2]) + g2 * sel3(a2, D0[0], D0[1], D0[2]);
+        E1 = g0 * sel3(a0, D1[0], D1[1], D1[2]) + g1 * sel3(a1, D1[0], D1[1], D1[2]) + g2 * sel3(a2, D1[0], D1[1], D1[2]);
+        E2 = g0 * sel3(a0, D2[0], D2[1], D2[2]) + g1 * sel3(a1, D2[0], D2[1], D2[2]) + g2 * sel3(a2, D2[0], D2[1], D2[2]);
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const int lj = a0 == j ? 0 : (a1 == j ? 1 : 2);  // path edge along axis j
+        const T gj = sel3(lj, g0, g1, g2);
+        T a = g0 * D0[j] + g1 * D1[j] + g2 * D2[j];  // h^2 grad lambda . grad u_j
+        T dj = gg;
+        if (FORM == FORM_SYM || (FORM == FORM_TR && cross)) {
+            a += sel3(lj, E0, E1, E2);
+            if (FORM == FORM_TR) a -= gj * hdiv;
+            else dj += gj * gj;
+        }
+        o.au[j] += wA * a;
+        o.dA[j] += wA * dj;
+        o.btp[j] -= wB * gj * pbar;
+    }
+}
+
+template <typename T>
+__device__ __forceinline__ T lane8_sum(T v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 4);
+    v += __shfl_xor_sync(0xffffffffu, v, 2);
+    v += __shfl_xor_sync(0xffffffffu, v, 1);
+    return v;
+}
+
+// Sum the partial rows of the 8 lanes of each group.  Must be reached by every lane of the
+// warp (no lane may have returned).
+template <typename T>
+__device__ __forceinline__ void lane8_reduce(GenRow<T>& o) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        o.au[j] = lane8_sum(o.au[j]);
+        o.dA[j] = lane8_sum(o.dA[j]);
+        o.btp[j] = lane8_sum(o.btp[j]);
+    }
+    o.bu = lane8_sum(o.bu);
+    o.cp = lane8_sum(o.cp);
+    o.dC = lane8_sum(o.dC);
+}
+
+template <typename T>
+__device__ __forceinline__ void genrow_zero(GenRow<T>& o) {
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { o.au[j] = 0; o.dA[j] = 0; o.btp[j] = 0; }
+    o.bu = 0; o.cp = 0; o.dC = 0;
+}
+
 }  // namespace sdx
