@@ -44,6 +44,7 @@ extern "C" {
 #define SDX_ENOCONV (-4)    /* maxit reached without meeting rtol; x holds the last iterate */
 #define SDX_ECUDA (-5)      /* a CUDA runtime call failed */
 #define SDX_ESINGULAR (-6)  /* the coarsest-grid matrix could not be factorised */
+#define SDX_ETIMEOUT (-7)   /* a bounded device-side wait gave up (the kernel returned early) */
 
 /* Boundary face types (Sec. 1, eq. boundary).  Faces are ordered -x, +x, -y, +y, -z, +z. */
 #define SDX_FACE_DIRICHLET 0 /* u = 0 */
@@ -196,6 +197,133 @@ int sdx_solve(sdx_hier_t h, const double* b, double* x, double rtol, int maxit, 
  * to library buffers, solves, copies x back, and synchronises the stream before returning. */
 int sdx_solve_host(sdx_hier_t h, const double* b_host, double* x_host, double rtol, int maxit,
                    int outer, int restart, sdx_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ batched solves
+ * A batch holds `count` independent problems (grid sizes, viscosity layouts and boundary
+ * faces may differ; form, coarse_form and prec must be the same) and advances them
+ * together: every phase of the V-cycle (a colour pass, the special rows of a colour, a
+ * residual, a transfer, the coarsest-grid solves) is one persistent launch over the work of
+ * all instances, the whole V-cycle is one CUDA graph, and the outer iteration is flexible
+ * GMRES per instance with all Krylov steps in lock step (converged instances drop out of
+ * every launch).  The arithmetic per instance is the one of sdx_vcycle / sdx_solve.
+ * Paper: Sec. 5 (V_var(3,3) Uzawa multigrid, direct coarse solve) applied to many problems;
+ * the batching itself has no counterpart in the paper. */
+typedef struct sdx_batch* sdx_batch_t; /* opaque, library-owned */
+
+/* Build the hierarchies of descs[0..count-1] (1 <= count <= 256) and the batch's own
+ * concatenated work vectors.  autotune != 0 times candidate block shapes (64..512 threads per
+ * block, persistent or one-block-per-tile grids) of the colour-pass and residual launches
+ * on every level and keeps the fastest.  Synchronous.  Errors as sdx_create, plus SDX_EINVAL
+ * when the descriptors disagree on form, coarse_form or prec.  On error *out is NULL. */
+int sdx_batch_create(const sdx_desc* descs, int count, int autotune, sdx_batch_t* out);
+
+/* Release the batch and every hierarchy in it (synchronises the device).  NULL is a no-op. */
+int sdx_batch_destroy(sdx_batch_t b);
+
+/* Finest-level size of one instance, as sdx_level_size(level 0). */
+int sdx_batch_size(sdx_batch_t b, int instance, int* n, int64_t* nodes, int64_t* free_dofs);
+
+/* Hierarchy of one instance, owned by the batch (valid until sdx_batch_destroy; never pass it
+ * to sdx_destroy).  It serves the queries, sdx_rhs, sdx_apply, sdx_residual, the transfers
+ * and the sdx_guess_* calls; calls that need the hierarchy's own work vectors (smoothers,
+ * V-cycles, solves) return SDX_EINVAL on it, since the batch keeps its own. */
+int sdx_batch_instance(sdx_batch_t b, int instance, sdx_hier_t* out);
+
+/* Block shape chosen for one batch level: threads per block and blocks of the colour-pass
+ * launches and of the residual launches (any output pointer may be NULL). */
+int sdx_batch_shape(sdx_batch_t b, int level, int* tpb_pass, int* grid_pass, int* tpb_residual,
+                    int* grid_residual);
+
+/* One V-cycle of every instance, in place: x[i] += M_i (b[i] - K_i x[i]), the same
+ * arithmetic as sdx_vcycle on each instance's own hierarchy.  b and x are HOST arrays of
+ * `count` DEVICE pointers to SoA vectors of each instance's finest level. */
+int sdx_batch_vcycle(sdx_batch_t b, const double* const* bvec, double* const* x, void* stream);
+
+/* Solve every instance to ||b_i - K_i x_i|| <= rtol ||b_i|| with FGMRES(restart)
+ * right-preconditioned by one V-cycle, starting from the x[i] passed in.  stats (may be
+ * NULL) receives `count` entries.  Synchronises the stream once per Krylov step.  Returns
+ * SDX_OK when every instance converged, SDX_ENOCONV if some hit maxit, SDX_ENONFINITE if a
+ * residual became NaN/Inf (per-instance status in stats).  b and x as in sdx_batch_vcycle. */
+int sdx_batch_solve(sdx_batch_t b, const double* const* bvec, double* const* x, double rtol,
+                    int maxit, int restart, sdx_stats* stats, void* stream);
+
+/* ------------------------------------------------------------------ learned initial guess
+ * A small 3D U-Net predicts an initial iterate from the viscosity layout and the forcing; the
+ * solver then runs to the same residual as from zero.  The paper has no counterpart.
+ * The network works on the n^3 cells (n a multiple of 4): tensors are [n^3][C] (cell
+ * i + n*(j + n*k), C channels contiguous), BF16 activations, FP32 accumulation.  Layers
+ * (3x3x3 convolutions, zero padding, weights [27][C_out][C_in], tap t = (dz+1)*9 + (dy+1)*3 +
+ * (dx+1) reading the input at offset (dx, dy, dz)):
+ *   a1 = relu(conv(x, 16->16)), a2 = relu(conv(a1, 16->16)),
+ *   a3 = relu(conv(pool(a2), 16->32)), a4 = relu(conv(a3, 32->32)),
+ *   a5 = relu(conv(pool(a4), 32->64)),
+ *   a6 = relu(conv(up(a5), 64->32) + a4), a7 = relu(conv(a6, 32->32)),
+ *   a8 = relu(conv(up(a7), 32->16) + a2), a9 = relu(conv(a8, 16->16)),
+ *   y  = conv(a9, 16->16)  (channels 0..3: u_x, u_y, u_z, p over the forcing scale)
+ * pool = mean of 2x2x2 cells, up = nearest neighbour; every convolution adds a bias.
+ * Parameters (221456 FP32 values) are stored layer by layer, W then b.  Input channels:
+ * log10 mu, the cell mean of the nodal forcing / fscale (3), 1, zeros (fscale = max |f|).
+ * Loss: sum over cells and channels 0..3 of (y - target)^2 / (4 n^3); optimiser: Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) on the mean gradient of each mini-batch.  Convolutions
+ * and weight gradients run on the tensor cores (tcgen05, BF16 in, FP32 accumulate). */
+typedef struct sdx_net* sdx_net_t; /* opaque, library-owned network with its optimiser state */
+
+/* Parameter count of the network (221456). */
+int64_t sdx_net_param_count(void);
+
+/* Create a network with He-normal weights drawn from `seed` and zero biases.  Synchronous. */
+int sdx_net_create(uint64_t seed, sdx_net_t* out);
+int sdx_net_destroy(sdx_net_t net);
+
+/* Copy the FP32 parameters to / from a HOST array of sdx_net_param_count() floats;
+ * sdx_net_set_params also resets the optimiser state.  Synchronous. */
+int sdx_net_get_params(sdx_net_t net, float* params_host);
+int sdx_net_set_params(sdx_net_t net, const float* params_host);
+
+/* y[n^3][16] (FP32, device) = network(x[n^3][16] (BF16 bit patterns, device)).  Synchronises
+ * the stream; SDX_ETIMEOUT if a tensor-core wait gave up. */
+int sdx_net_forward(sdx_net_t net, int n, const uint16_t* x, float* y, void* stream);
+
+/* Loss and gradient of one sample (x as above, target [n^3][16] FP32, device): *loss_host and
+ * grads_host (sdx_net_param_count() floats, may be NULL).  Synchronises the stream. */
+int sdx_net_loss_grad(sdx_net_t net, int n, const uint16_t* x, const float* target,
+                      double* loss_host, float* grads_host, void* stream);
+
+/* Train on `count` samples stored back to back (x: count x n^3 x 16 BF16, target: count x
+ * n^3 x 16 FP32, device) for `epochs` passes in seeded random order, Adam steps on
+ * mini-batches of `batch` samples with learning rate lr; loss_history_host (may be NULL)
+ * receives the mean loss of every epoch.  Synchronises once per epoch. */
+int sdx_net_train(sdx_net_t net, int n, int count, const uint16_t* x, const float* target,
+                  int epochs, int batch, float lr, uint64_t seed, double* loss_history_host,
+                  void* stream);
+
+/* The tensor-core convolution itself (for testing): y[n^3][cout] (FP32) = conv(x[n^3][cin],
+ * w[27][cout][cin]) + bias (may be NULL), ReLU if relu != 0; x and w BF16 bit patterns.
+ * Shapes (cin, cout) in {(16,16), (16,32), (32,16), (32,32), (32,64), (64,32)}.
+ * sdx_conv3_wgrad adds dw[t][co][ci] += sum_v dz[v][co] x[v + off_t][ci] (dz BF16 [n^3][cout],
+ * dw FP32).  Both synchronise the stream. */
+int sdx_conv3(int n, int cin, int cout, const uint16_t* x, const uint16_t* w, const float* bias,
+              int relu, float* y, void* stream);
+int sdx_conv3_wgrad(int n, int cin, int cout, const uint16_t* x, const uint16_t* dz, float* dw,
+                    void* stream);
+
+/* Network input of a hierarchy's finest grid (n a multiple of 4) from the nodal forcing f
+ * (device, 3 x (n+1)^3): x[n^3][16] (device, BF16) and *fscale_host = max |f| (1 if f = 0).
+ * Synchronises the stream. */
+int sdx_guess_features(sdx_hier_t h, const double* f_nodal, uint16_t* x, double* fscale_host,
+                       void* stream);
+
+/* Training target from a solution (device SoA vector of the finest level): t[n^3][16] (FP32)
+ * with the cell means of (u_x, u_y, u_z, p) / fscale in channels 0..3, zeros elsewhere. */
+int sdx_guess_target(sdx_hier_t h, const double* x_solution, double fscale, float* target,
+                     void* stream);
+
+/* Initial guess x0 (device SoA vector of the finest level) for the forcing f: features,
+ * network, then every node takes the mean of the prediction over its cells, times fscale;
+ * constrained components are zero.  Asynchronous; the network's scratch is sized for the
+ * last grid it saw (resizing synchronises the device). */
+int sdx_guess_predict(sdx_hier_t h, sdx_net_t net, const double* f_nodal, double* x0,
+                      void* stream);
 
 /* Number of CUDA kernels this library has launched in the process so far (all
  * hierarchies, all threads); used to count the kernels of a timed region. */

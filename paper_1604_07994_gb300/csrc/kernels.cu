@@ -6,7 +6,7 @@
 #include <string>
 
 #include "sdx_internal.h"
-#include "stencil.cuh"
+#include "bodies.cuh"
 
 namespace sdx {
 
@@ -19,20 +19,6 @@ inline unsigned blocks_for(long long count, int tpb = TPB) {
     return (unsigned)((count + tpb - 1) / tpb);
 }
 
-__device__ __forceinline__ void node_ijk(long long b, int n1, int& i, int& j, int& k) {
-    i = (int)(b % n1);
-    long long t = b / n1;
-    j = (int)(t % n1);
-    k = (int)(t / n1);
-}
-
-// Viscosity id of a uniform node: any of its eight cells, here the one with origin
-// (i-1, j-1, k-1), which sits at padded index (i, j, k).
-template <typename T>
-__device__ __forceinline__ int uniform_id(const LevelView<T>& L, int i, int j, int k) {
-    return L.cid[i + (long long)L.P * (j + (long long)L.P * k)];
-}
-
 // ------------------------------------------------------------------ apply / residual
 // y = K x (b == nullptr) or y = b - K x, for non-special nodes.
 template <typename T, int FORM>
@@ -40,158 +26,17 @@ __global__ void k_apply_uniform(LevelView<T> L, const T* __restrict__ x, T* __re
                                 const T* __restrict__ b) {
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= L.nn) return;
-    if (L.info[node] & INFO_SPECIAL) return;
-    int i, j, k;
-    node_ijk(node, L.n1, i, j, k);
-    const int id = uniform_id(L, i, j, k);
-    const T muh = L.muh[id];
-    const T tauh = L.tauh[id];
-    const T h2 = L.h * L.h;
-    const long long nn = L.nn;
-    Nb15<T> P;
-    load_nb15(x + 3 * nn, node, L, P);
-    T bu = 0;
-    Nb15<T> U[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        load_nb15(x + c * nn, node, L, U[c]);
-        bu += bstencil(U[c], c);
-    }
-#pragma unroll
-    for (int jj = 0; jj < 3; ++jj) {
-        T lap = T(6) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ));
-        if (FORM == FORM_SYM) {
-            lap += T(2) * U[jj].c - U[jj].S(jj);
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-                if (ii != jj) lap += xstencil(U[ii], ii, jj);
-        }
-        const T row = muh * lap - h2 * bstencil(P, jj);
-        y[jj * nn + node] = b ? b[jj * nn + node] - row : row;
-    }
-    const T cp = tauh * (T(6) * P.c - (P.S(EX) + P.S(EY) + P.S(EZ)));
-    const T rowp = h2 * bu - cp;
-    y[3 * nn + node] = b ? b[3 * nn + node] - rowp : rowp;
-}
-
-template <typename T, int FORM>
-__global__ void k_apply_general(LevelView<T> L, const int* __restrict__ list, int count,
-                                const T* __restrict__ x, T* __restrict__ y,
-                                const T* __restrict__ b) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const long long node = list[t];
-    int i, j, k;
-    node_ijk(node, L.n1, i, j, k);
-    const uint16_t inf = L.info[node];
-    const long long nn = L.nn;
-    if ((inf & 7) == 7) {  // all velocity components fixed: only the pressure row remains
-        T bu, cp, dC;
-        general_prow<T>(L, x, i, j, k, bu, cp, dC);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) y[c * nn + node] = T(0);
-        y[3 * nn + node] = b ? b[3 * nn + node] - (bu - cp) : bu - cp;
-        return;
-    }
-    GenRow<T> R;
-    general_row<T, FORM>(L, x, i, j, k, (inf & INFO_IFACE) != 0, R);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        T row = R.au[c] + R.btp[c];
-        T out = b ? b[c * nn + node] - row : row;
-        if (inf & (1u << c)) out = T(0);
-        y[c * nn + node] = out;
-    }
-    const T rowp = R.bu - R.cp;
-    y[3 * nn + node] = b ? b[3 * nn + node] - rowp : rowp;
+    apply_uniform_node<T, FORM>(L, node, x, y, b);
 }
 
 // ------------------------------------------------------------------ smoother passes
-// Colour pass thread mapping: blockIdx.y/z and threads over half rows.
-struct ColourIdx {
-    int i, j, k;
-    bool valid;
-};
-// Dense mapping of a 1-D grid onto the nodes of one colour: rows (j, k) of half = (n1+1)/2
-// slots, slot t of a row is node i = 2t + ((colour + j + k) & 1).
-__device__ __forceinline__ ColourIdx colour_node(int n1, int colour) {
-    ColourIdx c;
-    const int half = (n1 + 1) >> 1;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long row = t / half;
-    const int slot = (int)(t - row * half);
-    c.j = (int)(row % n1);
-    c.k = (int)(row / n1);
-    c.i = 2 * slot + ((colour + c.j + c.k) & 1);
-    c.valid = c.k < n1 && c.i < n1;
-    return c;
-}
-
-// Velocity update of non-special nodes of one colour: u_j += (f_j - (A u + B^T p)_j) / diag.
-// In place for a_tr / gradient form (rows read only other-colour velocities); the strain
-// form writes into `out` (3 components) because its cross-couplings read same-colour nodes.
+// Colour-pass kernels: one thread per colour slot (see colour_slot).
 template <typename T, int FORM>
 __global__ void k_vel_uniform(LevelView<T> L, int colour, T* __restrict__ x,
                               const T* __restrict__ f, T* __restrict__ out) {
-    ColourIdx ci = colour_node(L.n1, colour);
-    if (!ci.valid) return;
-    const long long node = ci.i + L.s1 * ci.j + L.s2 * ci.k;
-    if (L.info[node] & INFO_SPECIAL) return;
-    const int id = uniform_id(L, ci.i, ci.j, ci.k);
-    const T muh = L.muh[id];
-    const T inv = L.idA[id];
-    const T h2 = L.h * L.h;
-    const long long nn = L.nn;
-    Nb15<T> P;
-    load_nb15(x + 3 * nn, node, L, P);
-    if (FORM == FORM_SYM) {
-        Nb15<T> U[3];
-#pragma unroll
-        for (int c = 0; c < 3; ++c) load_nb15(x + c * nn, node, L, U[c]);
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-            T lap = T(8) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj);
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-                if (ii != jj) lap += xstencil(U[ii], ii, jj);
-            const T row = muh * lap - h2 * bstencil(P, jj);
-            out[jj * nn + node] = U[jj].c + (f[jj * nn + node] - row) * inv;
-        }
-    } else {
-#pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-            T* u = x + jj * nn;
-            const T c = u[node];
-            const T row = muh * lap7(u, node, L, c) - h2 * bstencil(P, jj);
-            u[node] = c + (f[jj * nn + node] - row) * inv;
-        }
-    }
-}
-
-// Special nodes of one colour: new velocity values into tmp[3 * t + c] (reads only values
-// from before the colour pass; scattered afterwards).
-template <typename T, int FORM>
-__global__ void k_vel_general(LevelView<T> L, const int* __restrict__ list, int count,
-                              const T* __restrict__ x, const T* __restrict__ f,
-                              T* __restrict__ tmp) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const long long node = list[t];
     int i, j, k;
-    node_ijk(node, L.n1, i, j, k);
-    const uint16_t inf = L.info[node];
-    GenRow<T> R;
-    general_row<T, FORM>(L, x, i, j, k, (inf & INFO_IFACE) != 0, R);
-    const long long nn = L.nn;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        T v = T(0);
-        if (!(inf & (1u << c))) {
-            const T cur = x[c * nn + node];
-            v = cur + (f[c * nn + node] - (R.au[c] + R.btp[c])) / R.dA[c];
-        }
-        tmp[3 * (long long)t + c] = v;
-    }
+    if (!colour_slot(L.n1, colour, (long long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+    vel_uniform_node<T, FORM>(L, i, j, k, x, f, out);
 }
 
 template <typename T>
@@ -199,165 +44,27 @@ __global__ void k_vel_scatter(const int* __restrict__ list, int count, const T* 
                               T* __restrict__ x, long long nn) {
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= count) return;
-    const long long node = list[t];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) x[c * nn + node] = tmp[3 * (long long)t + c];
+    vel_scatter_slot<T>(list, t, tmp, x, nn);
 }
 
 // strain form: copy the colour's new uniform-node values back
 template <typename T>
 __global__ void k_vel_copy_colour(LevelView<T> L, int colour, const T* __restrict__ src,
                                   T* __restrict__ x) {
-    ColourIdx ci = colour_node(L.n1, colour);
-    if (!ci.valid) return;
-    const long long node = ci.i + L.s1 * ci.j + L.s2 * ci.k;
-    if (L.info[node] & INFO_SPECIAL) return;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) x[c * L.nn + node] = src[c * L.nn + node];
+    int i, j, k;
+    if (!colour_slot(L.n1, colour, (long long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+    vel_copy_node<T>(L, i, j, k, src, x);
 }
 
-// Pressure Gauss-Seidel on C p = B u - g, relaxation OMEGA, non-special nodes of a colour.
 template <typename T>
 __global__ void k_pre_uniform(LevelView<T> L, int colour, T* __restrict__ x,
                               const T* __restrict__ g) {
-    ColourIdx ci = colour_node(L.n1, colour);
-    if (!ci.valid) return;
-    const long long node = ci.i + L.s1 * ci.j + L.s2 * ci.k;
-    if (L.info[node] & INFO_SPECIAL) return;
-    const int id = uniform_id(L, ci.i, ci.j, ci.k);
-    const T h2 = L.h * L.h;
-    const long long nn = L.nn;
-    T bu = 0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Nb15<T> U;
-        load_nb15(x + c * nn, node, L, U);
-        bu += bstencil(U, c);
-    }
-    T* p = x + 3 * nn;
-    const T pc = p[node];
-    const T cp = L.tauh[id] * lap7(p, node, L, pc);
-    const T s = h2 * bu - cp - g[node];
-    p[node] = pc + s * L.idC[id];
-}
-
-template <typename T, int FORM>
-__global__ void k_pre_general(LevelView<T> L, const int* __restrict__ list, int count,
-                              T* __restrict__ x, const T* __restrict__ g) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    const long long node = list[t];
     int i, j, k;
-    node_ijk(node, L.n1, i, j, k);
-    T bu, cp, dC;
-    general_prow<T>(L, x, i, j, k, bu, cp, dC);
-    T* p = x + 3 * L.nn;
-    const T s = bu - cp - g[node];
-    p[node] = p[node] + T(OMEGA) * s / dC;
-}
-
-// ------------------------------------------------------------------ special rows, 8 groups each
-// A block of 256 threads serves 32 consecutive rows of the list: warp w (0..7) evaluates the
-// tetrahedra w, w+8, w+16 of every row (lanes = rows, so loads stay coalesced along the list),
-// the 8 partial rows are summed in shared memory by warp 0, which writes the result.
-constexpr int SPEC_ROWS = 32;
-
-template <typename T>
-struct SpecPart {
-    T v[12][8][SPEC_ROWS];
-};
-
-template <typename T>
-__device__ __forceinline__ void spec_store(SpecPart<T>& sp, int w, int r, const GenRow<T>& R) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        sp.v[j][w][r] = R.au[j];
-        sp.v[3 + j][w][r] = R.dA[j];
-        sp.v[6 + j][w][r] = R.btp[j];
-    }
-    sp.v[9][w][r] = R.bu;
-    sp.v[10][w][r] = R.cp;
-    sp.v[11][w][r] = R.dC;
-}
-
-template <typename T>
-__device__ __forceinline__ void spec_sum(const SpecPart<T>& sp, int r, GenRow<T>& R) {
-    T acc[12];
-#pragma unroll
-    for (int f = 0; f < 12; ++f) {
-        T a = sp.v[f][0][r];
-#pragma unroll
-        for (int w = 1; w < 8; ++w) a += sp.v[f][w][r];
-        acc[f] = a;
-    }
-#pragma unroll
-    for (int j = 0; j < 3; ++j) { R.au[j] = acc[j]; R.dA[j] = acc[3 + j]; R.btp[j] = acc[6 + j]; }
-    R.bu = acc[9]; R.cp = acc[10]; R.dC = acc[11];
-}
-
-template <typename T, int FORM, int MODE>  // MODE 0: apply/residual, 1: velocity update, 2: pressure update
-__global__ void __launch_bounds__(256) k_special(LevelView<T> L, const int* __restrict__ list, int count,
-                                                 T* __restrict__ x, T* __restrict__ y,
-                                                 const T* __restrict__ b) {
-    __shared__ SpecPart<T> sp;
-    const int r = threadIdx.x & (SPEC_ROWS - 1);
-    const int w = threadIdx.x >> 5;
-    const int slot = blockIdx.x * SPEC_ROWS + r;
-    const bool valid = slot < count;
-    GenRow<T> R;
-    genrow_zero(R);
-    long long node = 0;
-    uint16_t inf = 7;
-    if (valid) {
-        node = list[slot];
-        inf = L.info[node];
-        int i, j, k;
-        node_ijk(node, L.n1, i, j, k);
-        const bool cross = (inf & INFO_IFACE) != 0;
-        const ArrayAcc<T> X{x, L.nn};
-        if (MODE == 2 || (inf & 7) == 7) {
-            for (int q = 0; q < 3; ++q) tet_row<T, FORM, true>(L, X, i, j, k, w + 8 * q, cross, R);
-        } else {
-            for (int q = 0; q < 3; ++q) tet_row<T, FORM, false>(L, X, i, j, k, w + 8 * q, cross, R);
-        }
-    }
-    spec_store(sp, w, r, R);
-    __syncthreads();
-    if (w != 0 || !valid) return;
-    spec_sum(sp, r, R);
-    const long long nn = L.nn;
-    if (MODE == 0) {  // y = K x, or y = b - K x
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const T row = R.au[c] + R.btp[c];
-            T out = b ? b[c * nn + node] - row : row;
-            if (inf & (1u << c)) out = T(0);
-            y[c * nn + node] = out;
-        }
-        const T rowp = R.bu - R.cp;
-        y[3 * nn + node] = b ? b[3 * nn + node] - rowp : rowp;
-    } else if (MODE == 1) {  // new velocity values into y = tmp[3 * slot + c]
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            T v = T(0);
-            if (!(inf & (1u << c)))
-                v = x[c * nn + node] + (b[c * nn + node] - (R.au[c] + R.btp[c])) / R.dA[c];
-            y[3 * (long long)slot + c] = v;
-        }
-    } else {  // pressure Gauss-Seidel in place, b = g
-        T* p = x + 3 * nn;
-        const T s = R.bu - R.cp - b[node];
-        p[node] = p[node] + T(OMEGA) * s / R.dC;
-    }
+    if (!colour_slot(L.n1, colour, (long long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
+    pre_uniform_node<T>(L, i, j, k, x, g);
 }
 
 // ------------------------------------------------------------------ special rows as stencils
-// The 15 Kuhn offsets of a node's stencil: 0, then +-e_x, +-e_y, +-e_z, +-(1,1,0), +-(1,0,1),
-// +-(0,1,1), +-(1,1,1).
-__device__ __constant__ signed char KOFF15[15][3] = {
-    {0, 0, 0}, {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}, {1, 1, 0},
-    {-1, -1, 0}, {1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, -1, -1}, {1, 1, 1}, {-1, -1, -1}};
-
 // Coefficients of special rows by evaluating the element-wise row on unit vectors: thread
 // (slot, col) with col = c * 15 + d applies the row of node list[slot] to the unit vector at
 // (component c, node + offset d).  rows: first row component stored (0 velocity / 3 pressure),
@@ -397,114 +104,30 @@ __global__ void k_d2f_plain(float* y, const double* x, long long count) {
     if (t < count) y[t] = (float)x[t];
 }
 
-// Special rows from their stored coefficients.  MODE 0: y = K x (or b - K x) on full rows;
-// MODE 3: the same on pressure-only rows (velocity rows written as 0); MODE 1: new velocity
-// values of a colour into tmp[3 * slot + r]; MODE 2: pressure Gauss-Seidel in place (b = g).
 template <typename T, int MODE>
 __global__ void k_spec_rows(LevelView<T> L, const int* __restrict__ list, int count,
                             const T* __restrict__ cf, T* __restrict__ x, T* __restrict__ y,
                             const T* __restrict__ b) {
     const int slot = blockIdx.x * blockDim.x + threadIdx.x;
     if (slot >= count) return;
-    const long long node = list[slot];
-    int i, j, k;
-    node_ijk(node, L.n1, i, j, k);
-    const uint16_t inf = L.info[node];
-    const long long nn = L.nn;
-    constexpr int NR = MODE == 0 ? 4 : (MODE == 1 ? 3 : 1);  // row components stored
-    T acc[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) acc[r] = T(0);
-#pragma unroll
-    for (int d = 0; d < 15; ++d) {
-        const int a = i + KOFF15[d][0], bb = j + KOFF15[d][1], cc = k + KOFF15[d][2];
-        if (a < 0 || bb < 0 || cc < 0 || a >= L.n1 || bb >= L.n1 || cc >= L.n1) continue;
-        const long long v = a + L.s1 * bb + L.s2 * cc;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const T xv = x[c * nn + v];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] += cf[(long long)(r * 60 + c * 15 + d) * count + slot] * xv;
-        }
-    }
-    if (MODE == 0) {
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            T out = b ? b[r * nn + node] - acc[r] : acc[r];
-            if (r < 3 && (inf & (1u << r))) out = T(0);
-            y[r * nn + node] = out;
-        }
-    } else if (MODE == 3) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) y[r * nn + node] = T(0);
-        y[3 * nn + node] = b ? b[3 * nn + node] - acc[0] : acc[0];
-    } else if (MODE == 1) {
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            T v = T(0);
-            if (!(inf & (1u << r)))
-                v = x[r * nn + node] + (b[r * nn + node] - acc[r]) / cf[(long long)(180 + r) * count + slot];
-            y[3 * (long long)slot + r] = v;
-        }
-    } else {
-        T* p = x + 3 * nn;
-        p[node] = p[node] + T(OMEGA) * (acc[0] - b[node]) / cf[(long long)60 * count + slot];
-    }
+    spec_row_slot<T, MODE>(L, list, count, cf, x, y, b, slot);
 }
 
 // ------------------------------------------------------------------ transfers
-__device__ __constant__ int KUHN14[14][3] = {
-    {1, 0, 0}, {-1, 0, 0}, {0, 1, 0}, {0, -1, 0}, {0, 0, 1}, {0, 0, -1}, {1, 1, 0},
-    {-1, -1, 0}, {1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, -1, -1}, {1, 1, 1}, {-1, -1, -1}};
-
-// b_c = P^T r_f : coarse node I gathers r_f(2I) + 1/2 sum_d r_f(2I + d) over the 14 Kuhn
-// edge directions (fine midpoints of the coarse edges at I).
 template <typename T>
 __global__ void k_restrict(LevelView<T> F, LevelView<T> C, const T* __restrict__ rf,
                            T* __restrict__ bc) {
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= C.nn) return;
-    int I, J, K;
-    node_ijk(node, C.n1, I, J, K);
-    const uint16_t inf = C.info[node];
-    const int fi = 2 * I, fj = 2 * J, fk = 2 * K;
-    const long long fb = fi + F.s1 * fj + F.s2 * fk;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const T* r = rf + c * F.nn;
-        T acc = 0;
-#pragma unroll
-        for (int d = 0; d < 14; ++d) {
-            const int a = fi + KUHN14[d][0], bb = fj + KUHN14[d][1], cc = fk + KUHN14[d][2];
-            if (a < 0 || bb < 0 || cc < 0 || a >= F.n1 || bb >= F.n1 || cc >= F.n1) continue;
-            acc += r[a + F.s1 * bb + F.s2 * cc];
-        }
-        T v = r[fb] + T(0.5) * acc;
-        if (c < 3 && (inf & (1u << c))) v = T(0);
-        bc[c * C.nn + node] = v;
-    }
+    restrict_node<T>(F, C, rf, bc, node);
 }
 
-// x_f += P e_c : fine node (2I+a, 2J+b, 2K+c) takes the mean of e_c at I and I+(a,b,c).
 template <typename T>
 __global__ void k_prolong_add(LevelView<T> F, LevelView<T> C, const T* __restrict__ ec,
                               T* __restrict__ xf) {
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= F.nn) return;
-    int i, j, k;
-    node_ijk(node, F.n1, i, j, k);
-    const uint16_t inf = F.info[node];
-    const int a = i & 1, b = j & 1, cz = k & 1;
-    const long long c0 = (i >> 1) + C.s1 * (j >> 1) + C.s2 * (k >> 1);
-    const long long c1 = c0 + a + C.s1 * b + C.s2 * cz;
-    const bool mid = (a | b | cz) != 0;
-#pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        if (c < 3 && (inf & (1u << c))) continue;
-        const T* e = ec + c * C.nn;
-        T v = mid ? T(0.5) * (e[c0] + e[c1]) : e[c0];
-        xf[c * F.nn + node] += v;
-    }
+    prolong_node<T>(F, C, ec, xf, node);
 }
 
 // ------------------------------------------------------------------ right-hand side

@@ -18,30 +18,6 @@ namespace sdx {
 static thread_local std::string g_last_error = "no error";
 void set_error(const std::string& msg) { g_last_error = msg; }
 
-struct Fail {
-    int code;
-};
-#define CK(call)                                                                          \
-    do {                                                                                  \
-        cudaError_t e_ = (call);                                                          \
-        if (e_ != cudaSuccess) {                                                          \
-            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                \
-            throw Fail{e_ == cudaErrorMemoryAllocation ? SDX_ENOMEM : SDX_ECUDA};          \
-        }                                                                                 \
-    } while (0)
-
-template <typename T>
-static T* dalloc(long long count) {
-    T* p = nullptr;
-    if (count <= 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)count);
-    if (e != cudaSuccess) {
-        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        throw Fail{SDX_ENOMEM};
-    }
-    return p;
-}
-
 template <>
 LevelView<double> view<double>(const Hier& H, int l) {
     const Level& L = H.lv[l];
@@ -308,7 +284,7 @@ static void build_coarse(Hier& H) {
     CK(cudaMemset(L.x, 0, sizeof(double) * 4 * nn));
 }
 
-static void free_hier(Hier* H) {
+void hier_free(Hier* H) {
     if (!H) return;
     cudaDeviceSynchronize();
     for (Level& L : H->lv) {
@@ -336,7 +312,7 @@ static void free_hier(Hier* H) {
     delete H;
 }
 
-static Hier* create(const sdx_desc* d) {
+Hier* hier_create(const sdx_desc* d) {
     if (!d || !d->cell_id || !d->mu) { set_error("null descriptor or array"); throw Fail{SDX_EINVAL}; }
     if (d->n < 2 || d->n_coarse < 2 || d->n > 2048) { set_error("n and n_coarse must be >= 2 (n <= 2048)"); throw Fail{SDX_EINVAL}; }
     {
@@ -419,7 +395,7 @@ static Hier* create(const sdx_desc* d) {
         build_coarse(*H);
         CK(cudaDeviceSynchronize());
     } catch (...) {
-        free_hier(H);
+        hier_free(H);
         throw;
     }
     return H;
@@ -660,13 +636,6 @@ static int solve(Hier& H, const double* b, double* x, double rtol, int maxit, in
 // ===================================================================== C ABI
 using namespace sdx;
 
-#define API_BEGIN try {
-#define API_END                                                  \
-    }                                                            \
-    catch (const Fail& f) { return f.code; }                     \
-    catch (const std::bad_alloc&) { set_error("host allocation failed"); return SDX_ENOMEM; } \
-    catch (...) { set_error("unexpected internal error"); return SDX_ECUDA; }
-
 static Hier* as_hier(sdx_hier_t h) { return reinterpret_cast<Hier*>(h); }
 
 static int check_level(Hier* H, int level) {
@@ -675,12 +644,11 @@ static int check_level(Hier* H, int level) {
     return SDX_OK;
 }
 
-static int launched(const char* what) {
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) {
-        set_error(std::string(what) + ": " + cudaGetErrorString(e));
-        return SDX_ECUDA;
-    }
+// Operations that use the hierarchy's own work vectors are refused on a batch instance.
+static int check_work(Hier* H, int level) {
+    const int c = check_level(H, level);
+    if (c) return c;
+    if (H->released) { set_error("this hierarchy belongs to a batch: use the sdx_batch_* calls"); return SDX_EINVAL; }
     return SDX_OK;
 }
 
@@ -690,14 +658,14 @@ int sdx_create(const sdx_desc* desc, sdx_hier_t* out) {
     if (!out) { set_error("null output pointer"); return SDX_EINVAL; }
     *out = nullptr;
     API_BEGIN
-    Hier* H = create(desc);
+    Hier* H = hier_create(desc);
     *out = reinterpret_cast<sdx_hier_t>(H);
     return SDX_OK;
     API_END
 }
 
 int sdx_destroy(sdx_hier_t h) {
-    free_hier(as_hier(h));
+    hier_free(as_hier(h));
     return SDX_OK;
 }
 
@@ -773,7 +741,7 @@ int sdx_rhs(sdx_hier_t h, const double* f, double* b, void* stream) {
 
 int sdx_uzawa(sdx_hier_t h, int level, const double* b, double* x, void* stream) {
     Hier* H = as_hier(h);
-    int c = check_level(H, level);
+    int c = check_work(H, level);
     if (c) return c;
     if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
     API_BEGIN
@@ -785,7 +753,7 @@ int sdx_uzawa(sdx_hier_t h, int level, const double* b, double* x, void* stream)
 int sdx_smooth_pass(sdx_hier_t h, int level, int which, int colour, const double* b, double* x,
                     void* stream) {
     Hier* H = as_hier(h);
-    int c = check_level(H, level);
+    int c = check_work(H, level);
     if (c) return c;
     if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
     if ((which != 0 && which != 1) || (colour != 0 && colour != 1)) { set_error("which and colour must be 0 or 1"); return SDX_EINVAL; }
@@ -810,7 +778,7 @@ int sdx_apply_f32(sdx_hier_t h, int level, const float* x, float* y, void* strea
 int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const float* b, float* x,
                         void* stream) {
     Hier* H = as_hier(h);
-    int c = check_level(H, level);
+    int c = check_work(H, level);
     if (c) return c;
     if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
     if ((which != 0 && which != 1) || (colour != 0 && colour != 1)) { set_error("which and colour must be 0 or 1"); return SDX_EINVAL; }
@@ -824,7 +792,7 @@ int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const fl
 int sdx_smooth_pass_noalloc(sdx_hier_t h, int level, int colour, const double* b, double* x,
                             void* stream) {
     Hier* H = as_hier(h);
-    int c = check_level(H, level);
+    int c = check_work(H, level);
     if (c) return c;
     if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
     if (colour != 0 && colour != 1) { set_error("colour must be 0 or 1"); return SDX_EINVAL; }
@@ -862,6 +830,7 @@ int sdx_prolong_add(sdx_hier_t h, int level, const double* ec, double* xf, void*
 int sdx_vcycle(sdx_hier_t h, const double* b, double* x, void* stream) {
     Hier* H = as_hier(h);
     if (!H || !b || !x) { set_error("null argument"); return SDX_EINVAL; }
+    if (int c = check_work(H, 0)) return c;
     API_BEGIN
     vcycle_inplace(*H, b, x, (cudaStream_t)stream);
     return launched("sdx_vcycle");
@@ -872,6 +841,7 @@ int sdx_solve(sdx_hier_t h, const double* b, double* x, double rtol, int maxit, 
               sdx_stats* stats, void* stream) {
     Hier* H = as_hier(h);
     if (!H || !b || !x) { set_error("null argument"); return SDX_EINVAL; }
+    if (int c = check_work(H, 0)) return c;
     if (!(rtol > 0) || maxit < 0 || (outer != SDX_OUTER_VCYCLE && outer != SDX_OUTER_FGMRES) ||
         (outer == SDX_OUTER_FGMRES && (restart < 1 || restart > 200))) {
         set_error("invalid rtol, maxit, outer or restart");
@@ -888,6 +858,7 @@ int sdx_solve_host(sdx_hier_t h, const double* b_host, double* x_host, double rt
                    int restart, sdx_stats* stats, void* stream) {
     Hier* H = as_hier(h);
     if (!H || !b_host || !x_host) { set_error("null argument"); return SDX_EINVAL; }
+    if (int c = check_work(H, 0)) return c;
     API_BEGIN
     cudaStream_t s = (cudaStream_t)stream;
     const size_t bytes = sizeof(double) * 4 * H->lv[0].nn;
@@ -914,6 +885,7 @@ const char* sdx_strerror(int code) {
         case SDX_ENOCONV: return "no convergence within maxit";
         case SDX_ECUDA: return "CUDA error";
         case SDX_ESINGULAR: return "singular coarse-grid matrix";
+        case SDX_ETIMEOUT: return "device-side wait timed out";
         default: return "unknown error";
     }
 }

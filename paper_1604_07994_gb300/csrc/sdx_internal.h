@@ -4,8 +4,11 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <new>
 #include <string>
 #include <vector>
+
+#include "../../include/sdx.h"
 
 namespace sdx {
 
@@ -19,8 +22,8 @@ constexpr uint16_t INFO_SPECIAL = 8;   // not (interior node with 8 cells of one
 constexpr uint16_t INFO_IFACE = 16;    // interface row: decoupled form adds cross-couplings
 constexpr uint8_t CELL_OUTSIDE = 255;  // id of the ghost cells around the domain
 
-constexpr double OMEGA = 0.3;
-constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle matrix (1.2 GB)          // pressure Gauss-Seidel relaxation (Sec. 5)
+constexpr double OMEGA = 0.3;  // pressure Gauss-Seidel relaxation (Sec. 5)
+constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle matrix (1.2 GB)
 
 // Read-only view of one level as seen by kernels, for arithmetic type T.
 template <typename T>
@@ -112,6 +115,7 @@ struct Hier {
     CycleGraph g64, g32;
     cudaStream_t cap = nullptr;     // internal stream used only to capture the graphs
     bool use_graph = true;
+    bool released = false;          // work vectors handed back (instance of a batch)
 };
 
 template <typename T>
@@ -169,5 +173,54 @@ long long launches_total();
 
 // error helper
 void set_error(const std::string& msg);
+
+// ---------------------------------------------------------------- host-side error handling
+// Internal failures throw Fail{code}; every extern "C" entry point catches them (API_BEGIN /
+// API_END) and returns the code.
+struct Fail {
+    int code;
+};
+#define CK(call)                                                                          \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            set_error(std::string(#call) + ": " + cudaGetErrorString(e_));                \
+            throw Fail{e_ == cudaErrorMemoryAllocation ? SDX_ENOMEM : SDX_ECUDA};          \
+        }                                                                                 \
+    } while (0)
+
+#define API_BEGIN try {
+#define API_END                                                                              \
+    }                                                                                        \
+    catch (const Fail& f) { return f.code; }                                                 \
+    catch (const std::bad_alloc&) { set_error("host allocation failed"); return SDX_ENOMEM; } \
+    catch (...) { set_error("unexpected internal error"); return SDX_ECUDA; }
+
+template <typename T>
+inline T* dalloc(long long count) {
+    T* p = nullptr;
+    if (count <= 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (size_t)count);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        throw Fail{SDX_ENOMEM};
+    }
+    return p;
+}
+
+// SDX_OK, or SDX_ECUDA with the message set if a launch since the last check failed.
+inline int launched(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error(std::string(what) + ": " + cudaGetErrorString(e));
+        return SDX_ECUDA;
+    }
+    return SDX_OK;
+}
+
+// Build / free one hierarchy (sdx_create / sdx_destroy without the C wrapper).  hier_create
+// throws Fail on error and leaves nothing allocated.
+Hier* hier_create(const sdx_desc* d);
+void hier_free(Hier* H);
 
 }  // namespace sdx

@@ -120,155 +120,16 @@ __device__ __forceinline__ void perm3(int s, int& a0, int& a1, int& a2) {
     }
 }
 
-// Accumulate the full row of node (bi, bj, bk) from its tetrahedra.  `cross` selects the
-// a_tr cross-couplings (interface rows); the strain form always adds its cross terms.
-template <typename T, int FORM>
-__device__ void general_row(const LevelView<T>& L, const T* __restrict__ x, int bi, int bj,
-                            int bk, bool cross, GenRow<T>& o) {
-    const T* ux = x;
-    const T* uy = x + L.nn;
-    const T* uz = x + 2 * L.nn;
-    const T* pp = x + 3 * L.nn;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) { o.au[j] = 0; o.dA[j] = 0; o.btp[j] = 0; }
-    o.bu = 0; o.cp = 0; o.dC = 0;
-    const T h = L.h;
-    const T wB = h * h / T(6);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
-        const int ox = bi - qx, oy = bj - qy, oz = bk - qz;  // cell origin
-        const uint8_t id = L.cid[(ox + 1) + (long long)L.P * ((oy + 1) + (long long)L.P * (oz + 1))];
-        const T mu = L.mu[id];
-        if (mu == T(0)) continue;
-        const T wA = mu * h / T(6);
-        const T wC = L.tau[id] * h / T(6);
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            int a0, a1, a2;
-            perm3(s, a0, a1, a2);
-            // b's position along the path
-            int qv[3] = {qx, qy, qz};
-            int m;
-            const int sum = qx + qy + qz;
-            if (sum == 0) m = 0;
-            else if (sum == 3) m = 3;
-            else if (sum == 1) { if (qv[a0] == 1) m = 1; else continue; }
-            else { if (qv[a2] == 0) m = 2; else continue; }
-            // vertex node indices along the path
-            long long v[4];
-            const long long base = ox + L.s1 * oy + L.s2 * oz;
-            const long long st[3] = {1, L.s1, L.s2};
-            v[0] = base;
-            v[1] = v[0] + st[a0];
-            v[2] = v[1] + st[a1];
-            v[3] = v[2] + st[a2];
-            T U[3][4], Pv[4];
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                U[0][t] = ux[v[t]]; U[1][t] = uy[v[t]]; U[2][t] = uz[v[t]]; Pv[t] = pp[v[t]];
-            }
-            // h grad u_c and h grad p: path edge l (1..3) runs along axis a_{l-1}
-            T hG[3][3], hP[3];
-            const int ax[3] = {a0, a1, a2};
-#pragma unroll
-            for (int l = 0; l < 3; ++l) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) hG[c][ax[l]] = U[c][l + 1] - U[c][l];
-                hP[ax[l]] = Pv[l + 1] - Pv[l];
-            }
-            const T hdiv = hG[0][0] + hG[1][1] + hG[2][2];
-            const T pbar = T(0.25) * (Pv[0] + Pv[1] + Pv[2] + Pv[3]);
-            // g = h grad lambda_m
-            T g[3] = {0, 0, 0};
-            if (m == 0) g[a0] = -1;
-            else if (m == 1) { g[a0] = 1; g[a1] = -1; }
-            else if (m == 2) { g[a1] = 1; g[a2] = -1; }
-            else g[a2] = 1;
-            const T gg = g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                T a = g[0] * hG[j][0] + g[1] * hG[j][1] + g[2] * hG[j][2];
-                T dj = gg;
-                if (FORM == FORM_SYM || (FORM == FORM_TR && cross)) {
-                    a += g[0] * hG[0][j] + g[1] * hG[1][j] + g[2] * hG[2][j];
-                    if (FORM == FORM_TR) a -= g[j] * hdiv;
-                    else dj += g[j] * g[j];
-                }
-                o.au[j] += wA * a;
-                o.dA[j] += wA * dj;
-                o.btp[j] -= wB * g[j] * pbar;
-            }
-            o.bu -= T(0.25) * wB * hdiv;
-            o.cp += wC * (g[0] * hP[0] + g[1] * hP[1] + g[2] * hP[2]);
-            o.dC += wC * gg;
-        }
-    }
-}
-
-// Pressure row only (B u, C p and diag C) of node (bi, bj, bk), from its tetrahedra.
-template <typename T>
-__device__ void general_prow(const LevelView<T>& L, const T* __restrict__ x, int bi, int bj, int bk,
-                             T& bu, T& cp, T& dC) {
-    const T* ux = x;
-    const T* uy = x + L.nn;
-    const T* uz = x + 2 * L.nn;
-    const T* pp = x + 3 * L.nn;
-    bu = 0; cp = 0; dC = 0;
-    const T h = L.h;
-    const T wB = h * h / T(6);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
-        const int ox = bi - qx, oy = bj - qy, oz = bk - qz;
-        const uint8_t id = L.cid[(ox + 1) + (long long)L.P * ((oy + 1) + (long long)L.P * (oz + 1))];
-        if (L.mu[id] == T(0)) continue;
-        const T wC = L.tau[id] * h / T(6);
-#pragma unroll
-        for (int s = 0; s < 6; ++s) {
-            int a0, a1, a2;
-            perm3(s, a0, a1, a2);
-            int qv[3] = {qx, qy, qz};
-            int m;
-            const int sum = qx + qy + qz;
-            if (sum == 0) m = 0;
-            else if (sum == 3) m = 3;
-            else if (sum == 1) { if (qv[a0] == 1) m = 1; else continue; }
-            else { if (qv[a2] == 0) m = 2; else continue; }
-            const long long st[3] = {1, L.s1, L.s2};
-            long long v[4];
-            v[0] = ox + L.s1 * oy + L.s2 * oz;
-            v[1] = v[0] + st[a0];
-            v[2] = v[1] + st[a1];
-            v[3] = v[2] + st[a2];
-            const T* uc[3] = {ux, uy, uz};
-            // h div u = sum over the path edges of the edge difference of the component along it
-            const T hdiv = (uc[a0][v[1]] - uc[a0][v[0]]) + (uc[a1][v[2]] - uc[a1][v[1]]) +
-                           (uc[a2][v[3]] - uc[a2][v[2]]);
-            T hP[3];
-            hP[a0] = pp[v[1]] - pp[v[0]];
-            hP[a1] = pp[v[2]] - pp[v[1]];
-            hP[a2] = pp[v[3]] - pp[v[2]];
-            T g[3] = {0, 0, 0};
-            if (m == 0) g[a0] = -1;
-            else if (m == 1) { g[a0] = 1; g[a1] = -1; }
-            else if (m == 2) { g[a1] = 1; g[a2] = -1; }
-            else g[a2] = 1;
-            bu -= T(0.25) * wB * hdiv;
-            cp += wC * (g[0] * hP[0] + g[1] * hP[1] + g[2] * hP[2]);
-            dC += wC * (g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-        }
-    }
-}
-
-// ------------------------------------------------------------------ 8 lanes per row
+// ------------------------------------------------------------------ element-wise rows
 // The 24 tetrahedra around a node as (position q of the node in the cell, with the cell's
 // origin at node - (q&1, q>>1&1, q>>2&1); axis permutation s of the Kuhn path; index m of the
-// node on that path).  Lane l of a row's 8-lane group takes entries l, l+8 and l+16.
+// node on that path).
+namespace {
 __device__ __constant__ signed char TET24[24][3] = {
     {0, 0, 0}, {0, 1, 0}, {0, 2, 0}, {0, 3, 0}, {0, 4, 0}, {0, 5, 0}, {1, 0, 1}, {1, 1, 1},
     {2, 2, 1}, {2, 3, 1}, {3, 0, 2}, {3, 2, 2}, {4, 4, 1}, {4, 5, 1}, {5, 1, 2}, {5, 4, 2},
     {6, 3, 2}, {6, 5, 2}, {7, 0, 3}, {7, 1, 3}, {7, 2, 3}, {7, 3, 3}, {7, 4, 3}, {7, 5, 3}};
+}  // namespace
 
 template <typename T>
 __device__ __forceinline__ T sel3(int i, T a, T b, T c) {
@@ -358,29 +219,6 @@ __device__ __forceinline__ void tet_row(const LevelView<T>& L, const Acc& X, int
         o.dA[j] += wA * dj;
         o.btp[j] -= wB * gj * pbar;
     }
-}
-
-template <typename T>
-__device__ __forceinline__ T lane8_sum(T v) {
-    v += __shfl_xor_sync(0xffffffffu, v, 4);
-    v += __shfl_xor_sync(0xffffffffu, v, 2);
-    v += __shfl_xor_sync(0xffffffffu, v, 1);
-    return v;
-}
-
-// Sum the partial rows of the 8 lanes of each group.  Must be reached by every lane of the
-// warp (no lane may have returned).
-template <typename T>
-__device__ __forceinline__ void lane8_reduce(GenRow<T>& o) {
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-        o.au[j] = lane8_sum(o.au[j]);
-        o.dA[j] = lane8_sum(o.dA[j]);
-        o.btp[j] = lane8_sum(o.btp[j]);
-    }
-    o.bu = lane8_sum(o.bu);
-    o.cp = lane8_sum(o.cp);
-    o.dC = lane8_sum(o.dC);
 }
 
 template <typename T>

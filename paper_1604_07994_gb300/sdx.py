@@ -17,7 +17,7 @@ import numpy as np
 _PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_PKG, "_lib", "libsdx.so")
 
-OK, EINVAL, ENOMEM, ENONFINITE, ENOCONV, ECUDA, ESINGULAR = 0, -1, -2, -3, -4, -5, -6
+OK, EINVAL, ENOMEM, ENONFINITE, ENOCONV, ECUDA, ESINGULAR, ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
 FACE_DIRICHLET, FACE_FREESLIP, FACE_TRACTION = 0, 1, 2
 FORM_DECOUPLED, FORM_STRAIN, FORM_GRADIENT = 0, 1, 2
 FORMS = {"tr": FORM_DECOUPLED, "decoupled": FORM_DECOUPLED, "sym": FORM_STRAIN,
@@ -30,7 +30,11 @@ EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_co
             "sdx_interface_mask", "sdx_apply", "sdx_residual", "sdx_rhs", "sdx_uzawa", "sdx_smooth_pass",
             "sdx_kernel_launches", "sdx_smooth_pass_noalloc", "sdx_apply_f32", "sdx_smooth_pass_f32",
             "sdx_restrict", "sdx_prolong_add", "sdx_vcycle", "sdx_solve", "sdx_solve_host",
-            "sdx_last_error", "sdx_strerror")
+            "sdx_batch_create", "sdx_batch_destroy", "sdx_batch_size", "sdx_batch_shape", "sdx_batch_instance",
+            "sdx_batch_vcycle", "sdx_batch_solve", "sdx_net_param_count", "sdx_net_create",
+            "sdx_net_destroy", "sdx_net_get_params", "sdx_net_set_params", "sdx_net_forward",
+            "sdx_net_loss_grad", "sdx_net_train", "sdx_conv3", "sdx_conv3_wgrad", "sdx_guess_features",
+            "sdx_guess_target", "sdx_guess_predict", "sdx_last_error", "sdx_strerror")
 
 
 class SdxError(RuntimeError):
@@ -86,11 +90,32 @@ def load() -> ctypes.CDLL:
         "sdx_vcycle": [P, P, P, P],
         "sdx_solve": [P, P, P, D, I, I, I, ctypes.POINTER(sdx_stats), P],
         "sdx_solve_host": [P, P, P, D, I, I, I, ctypes.POINTER(sdx_stats), P],
+        "sdx_batch_create": [ctypes.POINTER(sdx_desc), I, I, ctypes.POINTER(P)],
+        "sdx_batch_destroy": [P],
+        "sdx_batch_size": [P, I, ctypes.POINTER(I), ctypes.POINTER(L), ctypes.POINTER(L)],
+        "sdx_batch_shape": [P, I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I)],
+        "sdx_batch_vcycle": [P, P, P, P],
+        "sdx_batch_instance": [P, I, ctypes.POINTER(P)],
+        "sdx_batch_solve": [P, P, P, D, I, I, ctypes.POINTER(sdx_stats), P],
+        "sdx_net_create": [ctypes.c_uint64, ctypes.POINTER(P)],
+        "sdx_net_destroy": [P],
+        "sdx_net_get_params": [P, P],
+        "sdx_net_set_params": [P, P],
+        "sdx_net_forward": [P, I, P, P, P],
+        "sdx_net_loss_grad": [P, I, P, P, ctypes.POINTER(D), P, P],
+        "sdx_net_train": [P, I, I, P, P, I, I, ctypes.c_float, ctypes.c_uint64, P, P],
+        "sdx_conv3": [I, I, I, P, P, P, I, P, P],
+        "sdx_conv3_wgrad": [I, I, I, P, P, P, P],
+        "sdx_guess_features": [P, P, P, ctypes.POINTER(D), P],
+        "sdx_guess_target": [P, P, D, P, P],
+        "sdx_guess_predict": [P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
         fn.argtypes = args
         fn.restype = ctypes.c_int
+    lib.sdx_net_param_count.argtypes = []
+    lib.sdx_net_param_count.restype = ctypes.c_int64
     lib.sdx_kernel_launches.argtypes = []
     lib.sdx_kernel_launches.restype = ctypes.c_int64
     lib.sdx_last_error.argtypes = []
@@ -113,7 +138,7 @@ def _ptr(t, itemsize: int = 8) -> int:
     if isinstance(t, int):
         return t
     if t.dtype.itemsize != itemsize or not t.is_contiguous() or not t.is_cuda:
-        raise ValueError(f"vectors must be contiguous {8 * itemsize}-bit float CUDA tensors")
+        raise ValueError(f"tensors must be contiguous CUDA tensors of {8 * itemsize}-bit elements")
     return t.data_ptr()
 
 
@@ -126,6 +151,27 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
+def _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta):
+    """An sdx_desc for the arguments, plus the host arrays it points into (keep them alive)."""
+    cell = np.ascontiguousarray(np.asarray(cell_id, dtype=np.uint8).ravel())
+    mu_a = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
+    d = sdx_desc()
+    d.n, d.n_coarse = int(n), int(n_coarse)
+    d.cell_id = cell.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    d.mu = mu_a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.n_mu = int(mu_a.size)
+    for f in range(6):
+        d.face[f] = int(face[f])
+    d.form = FORMS[form] if isinstance(form, str) else int(form)
+    if coarse_form is None:
+        d.coarse_form = -1
+    else:
+        d.coarse_form = FORMS[coarse_form] if isinstance(coarse_form, str) else int(coarse_form)
+    d.prec = int(prec)
+    d.pspg_beta = float(beta)
+    return d, (cell, mu_a)
+
+
 class Hierarchy:
     """A grid hierarchy built by sdx_create (owned; freed by close() or on deletion)."""
 
@@ -133,22 +179,7 @@ class Hierarchy:
                  face: Sequence[int], form="tr", coarse_form=None, prec=PREC_FP64,
                  beta: float = 1.0 / 12.0):
         lib = load()
-        self._cell = np.ascontiguousarray(np.asarray(cell_id, dtype=np.uint8).ravel())
-        self._mu = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
-        d = sdx_desc()
-        d.n, d.n_coarse = int(n), int(n_coarse)
-        d.cell_id = self._cell.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
-        d.mu = self._mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
-        d.n_mu = int(self._mu.size)
-        for f in range(6):
-            d.face[f] = int(face[f])
-        d.form = FORMS[form] if isinstance(form, str) else int(form)
-        if coarse_form is None:
-            d.coarse_form = -1
-        else:
-            d.coarse_form = FORMS[coarse_form] if isinstance(coarse_form, str) else int(coarse_form)
-        d.prec = int(prec)
-        d.pspg_beta = float(beta)
+        d, self._keep = _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta)
         h = ctypes.c_void_p()
         _check(lib.sdx_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -161,6 +192,9 @@ class Hierarchy:
                    coarse_form, prec, beta)
 
     def close(self):
+        if getattr(self, "_borrowed", False):
+            self._h = None
+            return
         if getattr(self, "_h", None):
             load().sdx_destroy(self._h)
             self._h = None
@@ -247,6 +281,148 @@ class Hierarchy:
                                      int(maxit), int(outer), int(restart), ctypes.byref(st),
                                      _stream(stream)), allow)
         return st.as_dict()
+
+
+def _ptr_array(vectors, itemsize=8):
+    arr = (ctypes.c_void_p * len(vectors))()
+    for i, v in enumerate(vectors):
+        arr[i] = _ptr(v, itemsize)
+    return arr
+
+
+class Batch:
+    """Independent problems solved together by sdx_batch_* (owned; freed by close())."""
+
+    def __init__(self, problems, form="tr", coarse_form=None, prec=PREC_FP32_REFINED,
+                 beta: float = 1.0 / 12.0, autotune: bool = True):
+        lib = load()
+        descs = (sdx_desc * len(problems))()
+        self._keep = []
+        for i, p in enumerate(problems):
+            d, keep = _make_desc(p.n, p.n_coarse, p.cell_id, p.mu, p.face, form, coarse_form, prec, beta)
+            descs[i] = d
+            self._keep.append(keep)
+        h = ctypes.c_void_p()
+        _check(lib.sdx_batch_create(descs, len(problems), 1 if autotune else 0, ctypes.byref(h)))
+        self._h = h
+        self.count = len(problems)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sdx_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def sdx_batch_size(self, instance: int):
+        n, nodes, free = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().sdx_batch_size(self._h, instance, ctypes.byref(n), ctypes.byref(nodes), ctypes.byref(free)))
+        return n.value, nodes.value, free.value
+
+    def instance(self, i: int) -> "Hierarchy":
+        """The batch-owned hierarchy of instance i (queries, sdx_rhs, apply, sdx_guess_*)."""
+        h = ctypes.c_void_p()
+        _check(load().sdx_batch_instance(self._h, int(i), ctypes.byref(h)))
+        view = Hierarchy.__new__(Hierarchy)
+        view._h = h
+        view._owner = self  # keeps the batch alive; close() must not destroy it
+        view._borrowed = True
+        n, nodes, _ = self.sdx_batch_size(i)
+        view.n, view.nn = n, nodes
+        return view
+
+    def sdx_batch_shape(self, level: int):
+        v = [ctypes.c_int() for _ in range(4)]
+        _check(load().sdx_batch_shape(self._h, level, *[ctypes.byref(x) for x in v]))
+        return {"tpb_pass": v[0].value, "grid_pass": v[1].value, "tpb_residual": v[2].value,
+                "grid_residual": v[3].value}
+
+    def sdx_batch_vcycle(self, b_list, x_list, stream=None):
+        _check(load().sdx_batch_vcycle(self._h, _ptr_array(b_list), _ptr_array(x_list), _stream(stream)))
+
+    def sdx_batch_solve(self, b_list, x_list, rtol=1e-8, maxit=200, restart=30, stream=None,
+                        allow_noconv=False):
+        st = (sdx_stats * self.count)()
+        allow = (OK, ENOCONV) if allow_noconv else (OK,)
+        _check(load().sdx_batch_solve(self._h, _ptr_array(b_list), _ptr_array(x_list), float(rtol),
+                                      int(maxit), int(restart), st, _stream(stream)), allow)
+        return [st[i].as_dict() for i in range(self.count)]
+
+
+class Net:
+    """The learned-initial-guess network (sdx_net_*; owned, freed by close())."""
+
+    def __init__(self, seed: int = 0):
+        h = ctypes.c_void_p()
+        _check(load().sdx_net_create(int(seed), ctypes.byref(h)))
+        self._h = h
+        self.param_count = int(load().sdx_net_param_count())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sdx_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self) -> np.ndarray:
+        out = np.zeros(self.param_count, dtype=np.float32)
+        _check(load().sdx_net_get_params(self._h, out.ctypes.data))
+        return out
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != self.param_count:
+            raise ValueError("wrong parameter count")
+        _check(load().sdx_net_set_params(self._h, p.ctypes.data))
+
+    def forward(self, n, x_bf16, y_f32, stream=None):
+        _check(load().sdx_net_forward(self._h, int(n), _ptr(x_bf16, 2), _ptr(y_f32, 4), _stream(stream)))
+
+    def loss_grad(self, n, x_bf16, target_f32, stream=None):
+        loss = ctypes.c_double()
+        g = np.zeros(self.param_count, dtype=np.float32)
+        _check(load().sdx_net_loss_grad(self._h, int(n), _ptr(x_bf16, 2), _ptr(target_f32, 4),
+                                        ctypes.byref(loss), g.ctypes.data, _stream(stream)))
+        return loss.value, g
+
+    def train(self, n, count, x_bf16, target_f32, epochs, batch, lr, seed=0, stream=None):
+        hist = np.zeros(epochs, dtype=np.float64)
+        _check(load().sdx_net_train(self._h, int(n), int(count), _ptr(x_bf16, 2), _ptr(target_f32, 4),
+                                    int(epochs), int(batch), float(lr), int(seed), hist.ctypes.data,
+                                    _stream(stream)))
+        return hist
+
+    def predict(self, hier: "Hierarchy", f_nodal, x0, stream=None):
+        _check(load().sdx_guess_predict(hier._h, self._h, _ptr(f_nodal), _ptr(x0), _stream(stream)))
+
+
+def sdx_conv3(n, cin, cout, x_bf16, w_bf16, bias_f32, relu, y_f32, stream=None):
+    _check(load().sdx_conv3(int(n), int(cin), int(cout), _ptr(x_bf16, 2), _ptr(w_bf16, 2),
+                            _ptr(bias_f32, 4), int(relu), _ptr(y_f32, 4), _stream(stream)))
+
+
+def sdx_conv3_wgrad(n, cin, cout, x_bf16, dz_bf16, dw_f32, stream=None):
+    _check(load().sdx_conv3_wgrad(int(n), int(cin), int(cout), _ptr(x_bf16, 2), _ptr(dz_bf16, 2),
+                                  _ptr(dw_f32, 4), _stream(stream)))
+
+
+def sdx_guess_features(hier: "Hierarchy", f_nodal, x_bf16, stream=None) -> float:
+    fs = ctypes.c_double()
+    _check(load().sdx_guess_features(hier._h, _ptr(f_nodal), _ptr(x_bf16, 2), ctypes.byref(fs), _stream(stream)))
+    return fs.value
+
+
+def sdx_guess_target(hier: "Hierarchy", x_solution, fscale, target_f32, stream=None):
+    _check(load().sdx_guess_target(hier._h, _ptr(x_solution), float(fscale), _ptr(target_f32, 4), _stream(stream)))
 
 
 def sdx_kernel_launches() -> int:

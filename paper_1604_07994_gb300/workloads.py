@@ -294,3 +294,14 @@ def random_instance(n: int, n_coarse: int, seed: int, lattice: int, max_boxes: i
     ids = box_cell_ids(n, boxes)
     return Problem(n=n, n_coarse=n_coarse, cell_id=ids, mu=np.array([1.0, contrast]),
                    face=(DIRICHLET,) * 6, forcing=gaussian_blobs(seed), name=f"instance_{seed}_{n}")
+
+
+def batched_instances(count: int = 48, seed: int = 2024, sizes=(32, 48, 64, 96)) -> List[Problem]:
+    """The batched workload: `count` independent instances, grid size drawn uniformly from
+    `sizes` (cells per side), coarsest grid n/8 (so every instance has four levels), 1-4
+    seeded boxes on that coarsest lattice, contrast log-uniform in [1, 1e6], no-slip walls,
+    Gaussian-blob forcing."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    ns = rng.choice(np.asarray(sizes), size=count)
+    return [random_instance(int(n), int(n) // 8, seed * 1000 + k, int(n) // 8, forcing="blobs")
+            for k, n in enumerate(ns)]

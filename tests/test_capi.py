@@ -76,3 +76,29 @@ def test_strerror_and_argument_validation_without_a_device():
     assert lib.sdx_apply(None, 0, None, None, None) == sdx.EINVAL
     assert lib.sdx_destroy(None) == sdx.OK
 
+
+
+def test_batch_validation_without_a_device():
+    """sdx_batch_create refuses bad arguments before any CUDA call: no descriptors, a count
+    out of range, and instances that disagree on the form."""
+    from paper_1604_07994_gb300 import sdx
+    lib = ensure_built()
+    h = ctypes.c_void_p()
+    assert lib.sdx_batch_create(None, 1, 0, ctypes.byref(h)) == sdx.EINVAL
+    assert h.value is None
+    cells = np.zeros(8 ** 3, dtype=np.uint8)
+    mu = np.array([1.0])
+    descs = (sdx.sdx_desc * 2)()
+    for i, form in enumerate((sdx.FORM_DECOUPLED, sdx.FORM_STRAIN)):
+        d = descs[i]
+        d.n, d.n_coarse = 8, 2
+        d.cell_id = cells.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+        d.mu = mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        d.n_mu = 1
+        d.form, d.coarse_form, d.prec, d.pspg_beta = form, -1, 1, 1.0 / 12
+    assert lib.sdx_batch_create(descs, 0, 0, ctypes.byref(h)) == sdx.EINVAL
+    assert lib.sdx_batch_create(descs, 2, 0, ctypes.byref(h)) == sdx.EINVAL
+    assert b"same form" in lib.sdx_last_error()
+    assert h.value is None
+    assert lib.sdx_batch_destroy(None) == sdx.OK
+    assert lib.sdx_batch_solve(None, None, None, 1e-8, 10, 10, None, None) == sdx.EINVAL

@@ -1,0 +1,156 @@
+"""GPU parity of the learned-guess network (tensor-core convolutions, backward pass, optimiser,
+solver <-> network maps) against the FP64 oracle in oracle/nn.py.
+
+Tolerances.  A convolution multiplies BF16 operands exactly and accumulates in FP32 over
+K = 27 C_in (forward) or K = n^3 cells (weight gradient) terms, so with BF16-rounded inputs
+given to both sides the result agrees to FP32 accumulation error: 1e-3 of the largest output
+(a wrong operand layout or descriptor gives O(1) errors).  The whole network stores every
+activation in BF16 (unit roundoff 2^-9) through ten layers, so its loss and gradients are
+compared at 3e-2 (loss) and 8e-2 (relative Frobenius norm of each layer's gradient).
+"""
+import numpy as np
+import pytest
+
+from tests._lib import ensure_built
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle import nn as ON  # noqa: E402
+from paper_1604_07994_gb300 import workloads as W  # noqa: E402
+
+SHAPES = [(16, 16), (16, 32), (32, 16), (32, 32), (32, 64), (64, 32)]
+
+
+@pytest.fixture(scope="module")
+def sdx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    from paper_1604_07994_gb300 import sdx as mod
+    return mod
+
+
+def _bf16(a):
+    """(device BF16 tensor, the same values as FP64 numpy)"""
+    t = torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda().to(torch.bfloat16).contiguous()
+    return t, t.float().cpu().numpy().astype(np.float64)
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+@pytest.mark.parametrize("relu", [0, 1])
+@pytest.mark.parametrize("cin,cout", SHAPES)
+def test_conv3_matches_oracle(sdx, cin, cout, relu):
+    n = 12  # 1728 cells: 13.5 tiles of 128, a ragged last tile
+    r = _rng(cin * 100 + cout + relu)
+    xd, x = _bf16(r.standard_normal((n ** 3, cin)))
+    wd, w = _bf16(r.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    b = r.standard_normal(cout).astype(np.float32)
+    y = torch.empty((n ** 3, cout), dtype=torch.float32, device="cuda")
+    sdx.sdx_conv3(n, cin, cout, xd, wd, torch.from_numpy(b).cuda(), relu, y)
+    ref = ON.conv3(x, w, n, b.astype(np.float64))
+    if relu:
+        ref = np.maximum(ref, 0.0)
+    got = y.cpu().numpy()
+    assert np.abs(got - ref).max() <= 1e-3 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("cin,cout", SHAPES)
+def test_conv3_wgrad_matches_oracle(sdx, cin, cout):
+    n = 12
+    r = _rng(7 * cin + cout)
+    xd, x = _bf16(r.standard_normal((n ** 3, cin)))
+    dzd, dz = _bf16(r.standard_normal((n ** 3, cout)))
+    dw = torch.zeros((27, cout, cin), dtype=torch.float32, device="cuda")
+    sdx.sdx_conv3_wgrad(n, cin, cout, xd, dzd, dw)
+    ref = ON.conv3_wgrad(x, dz, n)
+    assert np.abs(dw.cpu().numpy() - ref).max() <= 1e-3 * np.abs(ref).max()
+
+
+def _flat(params):
+    return np.concatenate([np.concatenate([params[name][0].ravel(), params[name][1]]) for name, *_ in ON.LAYERS])
+
+
+def _unflat(vec):
+    out, o = {}, 0
+    for name, ci, co, _ in ON.LAYERS:
+        w = vec[o:o + 27 * co * ci].reshape(27, co, ci)
+        o += 27 * co * ci
+        out[name] = (w, vec[o:o + co])
+        o += co
+    return out
+
+
+def test_network_loss_and_gradients_match_oracle(sdx):
+    n = 8
+    r = _rng(3)
+    P = ON.init_params(5)
+    P = {k: (w, 0.05 * r.standard_normal(b.shape)) for k, (w, b) in P.items()}
+    net = sdx.Net(1)
+    assert net.param_count == sum(w.size + b.size for w, b in P.values()) == 221456
+    net.set_params(_flat(P))
+    # the GPU multiplies BF16 weights: give the oracle the same rounded values
+    Pr = _unflat(_flat(P))
+    Pr = {k: (_bf16(w)[1], b) for k, (w, b) in Pr.items()}
+    xd, x = _bf16(np.concatenate([r.standard_normal((n ** 3, 5)), np.zeros((n ** 3, 11))], axis=1))
+    tgt = r.standard_normal((n ** 3, 16)).astype(np.float32)
+    loss, g = net.loss_grad(n, xd, torch.from_numpy(tgt).cuda())
+    y, cache = ON.forward(Pr, x, n)
+    lref, dy = ON.loss_and_grad_y(y, tgt.astype(np.float64))
+    G = ON.backward(Pr, cache, dy, n)
+    assert abs(loss - lref) <= 3e-2 * lref
+    gg = _unflat(g.astype(np.float64))
+    for name in G:
+        for a, b in zip(gg[name], G[name]):
+            assert np.linalg.norm(a - b) <= 8e-2 * np.linalg.norm(b), name
+    # forward alone gives the same prediction
+    yd = torch.empty((n ** 3, 16), dtype=torch.float32, device="cuda")
+    net.forward(n, xd, yd)
+    assert np.linalg.norm(yd.cpu().numpy() - y) <= 3e-2 * np.linalg.norm(y)
+
+
+def test_adam_training_step_matches_oracle(sdx):
+    """One mini-batch of one sample: the GPU's Adam step equals the oracle's Adam step applied
+    to the GPU's own gradient (first step: the update is -lr * sign(g) up to eps)."""
+    n = 8
+    r = _rng(9)
+    net = sdx.Net(2)
+    w0 = net.get_params()
+    xd, _ = _bf16(np.concatenate([r.standard_normal((n ** 3, 5)), np.zeros((n ** 3, 11))], axis=1))
+    tgt = torch.from_numpy(r.standard_normal((n ** 3, 16)).astype(np.float32)).cuda()
+    _, g = net.loss_grad(n, xd, tgt)
+    net.set_params(w0)
+    net.train(n, 1, xd, tgt, epochs=1, batch=1, lr=1e-3)
+    w1 = net.get_params()
+    ref, _, _ = ON.adam_step(w0.astype(np.float64), g.astype(np.float64), 0 * g, 0 * g, 1, 1e-3)
+    assert np.abs(w1 - ref).max() <= 1e-6
+
+
+def test_solver_network_maps_match_oracle(sdx):
+    p = W.random_instance(12, 3, 4, 3, forcing="blobs")
+    H = sdx.Hierarchy.from_problem(p)
+    f = p.nodal_forcing()
+    fd = torch.from_numpy(f.ravel().copy()).cuda()
+    xb = torch.empty((12 ** 3, 16), dtype=torch.bfloat16, device="cuda")
+    fs = sdx.sdx_guess_features(H, fd, xb)
+    ref, fs_ref = ON.features(p.cell_mu().ravel(), f, 12)
+    assert fs == fs_ref
+    assert np.abs(xb.float().cpu().numpy() - ref).max() <= 2 ** -8 * np.abs(ref).max()
+    sol = W.random_vector(12, 3).ravel()
+    con = H.sdx_constraint_mask(0)
+    sol[con] = 0.0
+    t = torch.empty((12 ** 3, 16), dtype=torch.float32, device="cuda")
+    sdx.sdx_guess_target(H, torch.from_numpy(sol).cuda(), fs, t)
+    tref = ON.target(sol, fs, 12)
+    assert np.abs(t.cpu().numpy() - tref).max() <= 1e-6 * np.abs(tref).max()
+    # predict = features -> network -> nodes
+    net = sdx.Net(3)
+    x0 = torch.empty(4 * p.nodes, dtype=torch.float64, device="cuda")
+    net.predict(H, fd, x0)
+    y = torch.empty((12 ** 3, 16), dtype=torch.float32, device="cuda")
+    net.forward(12, xb, y)
+    x0ref = ON.to_nodes(y.cpu().numpy().astype(np.float64), fs, 12, con)
+    assert np.abs(x0.cpu().numpy() - x0ref).max() <= 1e-6 * max(np.abs(x0ref).max(), 1e-30)
