@@ -40,13 +40,24 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per side (workload size)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep"],
-                    help="sweep: only time the operator apply and smoother passes (profiling)")
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "guess", "batch", "paper", "conv"],
+                    help="sweep: only time the operator apply and smoother passes (profiling); "
+                         "guess: only the learned-initial-guess experiment; batch: only the batched workload")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="arithmetic of --mode sweep")
     ap.add_argument("--form", default="tr", choices=["tr", "sym", "grad"])
     ap.add_argument("--maxit", type=int, default=500,
                     help="iteration cap per solve (profiling runs use a small cap)")
     ap.add_argument("--no-details", action="store_true", help="skip sweeps, e2e, variants, CPU leg")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 48-instance batched workload")
+    ap.add_argument("--no-layer", action="store_true", help="skip the 256^3 mixed-precision workload")
+    ap.add_argument("--no-guess", action="store_true", help="skip the learned-initial-guess experiment")
+    ap.add_argument("--no-paper", action="store_true", help="skip the paper's columns problem (time per cycle, rate)")
+    ap.add_argument("--guess-samples", type=int, default=192, help="training solves at 64^3")
+    ap.add_argument("--guess-epochs", type=int, default=12)
+    ap.add_argument("--guess-eval", type=int, default=4, help="unseen 128^3 instances to evaluate")
+    ap.add_argument("--guess-smooth", default="4", help="comma-separated Uzawa smoothing steps applied to the guess")
+    ap.add_argument("--batch-count", type=int, default=48, help="instances of the batched workload")
+    ap.add_argument("--conv-n", type=int, default=64, help="cells per side of --mode conv")
     return ap.parse_args()
 
 
@@ -173,6 +184,13 @@ def main():
     if args.mode == "sweep":
         run_sweeps(args)
         return
+    if args.mode in ("guess", "batch", "paper", "conv"):
+        import torch
+        torch.cuda.set_device(0)
+        from paper_1604_07994_gb300 import sdx
+        out = {"guess": run_guess, "batch": run_batch, "paper": run_paper, "conv": run_conv}[args.mode](args, sdx, torch)
+        print(json.dumps({"mode": args.mode, **out}), flush=True)
+        return
     import torch
     ws, rank, local = dist_env()
     torch.cuda.set_device(local)
@@ -187,7 +205,9 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream()
     t0 = time.perf_counter()
-    H = sdx.Hierarchy.from_problem(prob, form="tr", prec=sdx.PREC_FP64)
+    # decoupled operator a_tr on the finest level; the coarser levels use a_sym (the coarse-grid
+    # swap of Sec. 5 extended to every coarse level), FP64 throughout
+    H = sdx.Hierarchy.from_problem(prob, form="tr", coarse_form="sym", prec=sdx.PREC_FP64)
     setup_s = time.perf_counter() - t0
     _, nodes, free = H.sdx_level_size(0)
     f = torch.from_numpy(prob.nodal_forcing().ravel()).to(dev)
@@ -259,7 +279,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"three_boxes_{n}: {n}^3 cells ({free} free DoF), 3 seeded boxes on the 1/8 lattice, mu ratio 1e4, no-slip walls, manufactured forcing",
-                   "form": "decoupled (a_tr with interface strain rows)", "solver": f"FGMRES({RESTART}) + V_var(3,3) Uzawa multigrid, 5 levels, coarsest 8^3 dense FP64 inverse",
+                   "form": "decoupled (a_tr with interface strain rows) on the finest level, a_sym on the coarser levels",
+                   "solver": f"FGMRES({RESTART}) + V_var(3,3) Uzawa multigrid, 5 levels, coarsest 8^3 dense FP64 inverse",
                    "rtol": 1e-8, "time_to_1e8_s": ms * 1e-3, "iterations": iters, "final_rel_res": final_res,
                    "setup_s": setup_s, "l2": "inputs larger than L2 (each 4-component FP64 vector is 69 MB; solver working set > 4 GB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
@@ -330,20 +351,21 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
     if not args.no_variants:
         var = {}
         for name, form, prec, cform in (("strain_fp64", "sym", sdx.PREC_FP64, None),
-                                        ("decoupled_fp32_refined", "tr", sdx.PREC_FP32_REFINED, None),
+                                        ("decoupled_tr_coarse_fp64", "tr", sdx.PREC_FP64, None),
+                                        ("decoupled_fp32_refined", "tr", sdx.PREC_FP32_REFINED, "sym"),
                                         ("strain_fp32_refined", "sym", sdx.PREC_FP32_REFINED, None),
-                                        ("decoupled_symcoarse_fp64", "tr", sdx.PREC_FP64, "sym"),
-                                        ("decoupled_symcoarse_fp32_refined", "tr", sdx.PREC_FP32_REFINED, "sym")):
+                                        ("decoupled_tr_coarse_fp32_refined", "tr", sdx.PREC_FP32_REFINED, None)):
             H2 = sdx.Hierarchy.from_problem(prob, form=form, prec=prec, coarse_form=cform)
             x2 = torch.zeros_like(b)
             st = H2.sdx_solve(b, x2, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)
             reps2 = 2
             tt = _time(lambda: (x2.zero_(), H2.sdx_solve(b, x2, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)), reps2, stream, torch)
             st = H2.sdx_solve(b, x2.zero_(), rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)
-            dx = float(torch.linalg.norm(x2 - x) / torch.linalg.norm(x)) if form == "tr" else None
+            dx = solution_diff(x2, x, nn) if form == "tr" else None
             var[name] = {"time_to_1e8_s": tt * 1e-3, "gdofs": free / (tt * 1e-3) / 1e9,
                          "iterations": st["iterations"], "final_rel_res": st["res"] / st["bnorm"],
-                         "rel_l2_diff_vs_fp64_solution": dx}
+                         "coarse_levels": cform or form,
+                         "rel_l2_diff_vs_headline_solution": dx}
             if form == "sym":
                 ta = _time(lambda: H2.sdx_apply(0, xr, y), reps, stream, torch)
                 tv = _time(lambda: H2.sdx_smooth_pass(0, 0, 0, b, xs), reps, stream, torch)
@@ -351,8 +373,203 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
                 var[name]["velocity_pass_ms"] = tv
             H2.close()
         out["variants"] = var
+    if not args.no_layer:
+        out["top_layer_256"] = run_layer(args, sdx, torch, W, stream)
+    if not args.no_batch:
+        out["batched_48"] = run_batch(args, sdx, torch)
+    if not args.no_guess:
+        out["learned_guess"] = run_guess(args, sdx, torch)
+    if not args.no_paper:
+        out["paper_columns"] = run_paper(args, sdx, torch)
     if not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         out["cpu_baseline"] = oracle_sample()
+    return out
+
+
+def solution_diff(xa, xb, nn):
+    """Relative L2 difference of two solutions after removing the difference's pressure mean
+    (without a traction face the pressure is determined up to a constant)."""
+    d = xa - xb
+    d[3 * nn:] -= d[3 * nn:].mean()
+    return float(d.norm() / xb.norm())
+
+
+def run_layer(args, sdx, torch, W, stream):
+    """256^3 cells, top layer z >= 7/8 of viscosity 1e3, traction-free top, free-slip sides,
+    no-slip bottom, Gaussian-blob buoyancy: FP64 cycles vs FP32 cycles in FP64 refinement,
+    decoupled form (a_sym on the coarse levels), FGMRES to 1e-8."""
+    prob = W.top_layer(256, 8)
+    f = torch.from_numpy(prob.nodal_forcing().ravel()).cuda()
+    res = {"workload": "top_layer_256: 256^3 cells, layer z >= 7/8 mu 1e3 over mu 1, traction top, free-slip sides, no-slip bottom, Gaussian-blob forcing"}
+    sols = {}
+    for name, prec in (("fp64", sdx.PREC_FP64), ("fp32_refined", sdx.PREC_FP32_REFINED)):
+        t0 = time.perf_counter()
+        H = sdx.Hierarchy.from_problem(prob, form="tr", coarse_form="sym", prec=prec)
+        setup = time.perf_counter() - t0
+        _, nn, free = H.sdx_level_size(0)
+        b = torch.zeros(4 * nn, dtype=torch.float64, device="cuda")
+        H.sdx_rhs(f, b)
+        x = torch.zeros_like(b)
+        st = H.sdx_solve(b, x, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)
+        tt = _time(lambda: (x.zero_(), H.sdx_solve(b, x, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)), 2, stream, torch)
+        res[name] = {"time_to_1e8_s": tt * 1e-3, "gdofs": free / (tt * 1e-3) / 1e9, "iterations": st["iterations"],
+                     "final_rel_res": st["res"] / st["bnorm"], "free_dofs": free, "setup_s": setup}
+        sols[name] = x
+        H.close()
+    d = sols["fp32_refined"] - sols["fp64"]
+    res["fp32_refined"]["rel_l2_diff_vs_fp64_solution"] = float(d.norm() / sols["fp64"].norm())
+    res["speedup_fp32_refined_vs_fp64"] = res["fp64"]["time_to_1e8_s"] / res["fp32_refined"]["time_to_1e8_s"]
+    return res
+
+
+def run_batch(args, sdx, torch, count=None):
+    """48 independent instances, sizes uniform in {32,48,64,96}^3, 1-4 boxes, contrast
+    log-uniform in [1, 1e6], Gaussian-blob forcing; FP32 cycles in FP64 refinement, decoupled
+    form (a_sym on the coarse levels); one batch (persistent launches, graph-captured cycle,
+    autotuned block shapes) vs the same instances solved one after another."""
+    from paper_1604_07994_gb300 import workloads as W
+    count = count or args.batch_count
+    probs = W.batched_instances(count)
+    t0 = time.perf_counter()
+    B = sdx.Batch(probs, prec=sdx.PREC_FP32_REFINED, coarse_form="sym", autotune=True)
+    setup = time.perf_counter() - t0
+    bs, xs, free = [], [], 0
+    for i, p in enumerate(probs):
+        H = B.instance(i)
+        free += H.sdx_level_size(0)[2]
+        f = torch.from_numpy(p.nodal_forcing().ravel()).cuda()
+        b = torch.zeros(4 * p.nodes, dtype=torch.float64, device="cuda")
+        H.sdx_rhs(f, b)
+        bs.append(b)
+        xs.append(torch.zeros_like(b))
+    st = B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=400, restart=30)
+    torch.cuda.synchronize()
+    l0 = sdx.sdx_kernel_launches()
+    ts = []
+    for _ in range(3):
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        st = B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=400, restart=30)
+        torch.cuda.synchronize()
+        ts.append(time.perf_counter() - t1)
+    launches = (sdx.sdx_kernel_launches() - l0) / 3
+    its = [s["iterations"] for s in st]
+    shapes = [B.sdx_batch_shape(lv) for lv in range(4)]
+    tb = min(ts)
+    # the same instances, one hierarchy after another (same solver settings)
+    tseq, its_seq = 0.0, []
+    for p, b in zip(probs, bs):
+        H = sdx.Hierarchy.from_problem(p, form="tr", coarse_form="sym", prec=sdx.PREC_FP32_REFINED)
+        x = torch.zeros_like(b)
+        H.sdx_solve(b, x, rtol=1e-8, maxit=400, outer=sdx.OUTER_FGMRES, restart=30)
+        x.zero_()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s1 = H.sdx_solve(b, x, rtol=1e-8, maxit=400, outer=sdx.OUTER_FGMRES, restart=30)
+        torch.cuda.synchronize()
+        tseq += time.perf_counter() - t1
+        its_seq.append(s1["iterations"])
+        H.close()
+    B.close()
+    return {"workload": f"{count} instances, sizes {sorted(set(p.n for p in probs))}^3 cells, 1-4 boxes, contrast log-uniform in [1, 1e6], Gaussian-blob forcing",
+            "total_free_dofs": int(free), "time_to_1e8_s": tb, "gdofs": free / tb / 1e9, "all_converged": all(s["status"] == 0 for s in st),
+            "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)), "setup_s": setup,
+            "gpu_launches_per_solve": int(launches), "block_shapes_per_level": shapes,
+            "sequential_single_solves_s": tseq, "sequential_iterations_mean": float(np.mean(its_seq)),
+            "speedup_batched_vs_sequential": tseq / tb}
+
+
+def run_paper(args, sdx, torch, cycles=40):
+    """The paper's own measurement (Sec. 5, Table timeANDconv): the viscosity-columns problem
+    with free-slip faces at levels 5 (128^3 cells) and 6 (256^3), time of one V_var(3,3) cycle
+    and the asymptotic residual reduction rate rho for the strain, decoupled ("modified
+    stencil") and gradient forms.  rho: plain V-cycles x <- x + M(0 - K x) from a seeded random
+    x, the residual renormalised every cycle, geometric mean of the last 10 reductions."""
+    from paper_1604_07994_gb300 import workloads as W
+    out = {"problem": "viscosity columns (Sec. 4.2.4), free-slip faces, coarsest grid 8^3, FP64",
+           "paper_xeon_32_cores": {"L5": {"strain": [1.18, 0.296], "decoupled": [1.12, 0.244], "gradient": [1.34, 0.240]},
+                                   "L6": {"strain": [3.02, 0.280], "decoupled": [2.45, 0.242], "gradient": [2.64, 0.240]},
+                                   "columns": "[seconds per V_var(3,3) cycle, rho]"}}
+    for lvl, n in (("L5", 128), ("L6", 256)):
+        prob = W.viscosity_columns(n, 8)
+        res = {}
+        for name, form in (("strain", "sym"), ("decoupled", "tr"), ("gradient", "grad")):
+            H = sdx.Hierarchy.from_problem(prob, form=form, prec=sdx.PREC_FP64)
+            _, nn, _ = H.sdx_level_size(0)
+            con = torch.from_numpy(H.sdx_constraint_mask(0)).cuda()
+            x = torch.from_numpy(W.random_vector(n, 77).ravel()).cuda()
+            x[con] = 0
+            zero = torch.zeros_like(x)
+            r = torch.empty_like(x)
+            rates = []
+            H.sdx_residual(0, zero, x, r)
+            prev = float(torch.linalg.norm(r))
+            for _ in range(cycles):
+                H.sdx_vcycle(zero, x)
+                H.sdx_residual(0, zero, x, r)
+                cur = float(torch.linalg.norm(r))
+                rates.append(cur / prev)
+                x /= cur
+                prev = 1.0
+            rho = float(np.exp(np.mean(np.log(rates[-10:]))))
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                H.sdx_vcycle(zero, x)
+            e1.record()
+            torch.cuda.synchronize()
+            res[name] = {"seconds_per_cycle": e0.elapsed_time(e1) / 5e3, "rho": rho}
+            H.close()
+        out[lvl] = res
+    return out
+
+
+def run_conv(args, sdx, torch):
+    """The network alone on an n^3 cell grid: time of one forward pass and of one forward +
+    backward pass (loss and all gradients) from seeded random inputs; algorithmic tensor
+    flops = sum over layers of 2 * cells * 27 * C_in * C_out (forward), three times that with
+    the backward pass (input and weight gradients)."""
+    n = args.conv_n
+    rng = np.random.Generator(np.random.PCG64(12))
+    V = n ** 3
+    x = torch.from_numpy(rng.standard_normal((V, 16)).astype(np.float32)).cuda().to(torch.bfloat16)
+    t = torch.from_numpy(rng.standard_normal((V, 16)).astype(np.float32)).cuda()
+    y = torch.empty((V, 16), dtype=torch.float32, device="cuda")
+    net = sdx.Net(seed=5)
+    layers = [(16, 16, 0), (16, 16, 0), (16, 32, 1), (32, 32, 1), (32, 64, 2), (64, 32, 1), (32, 32, 1),
+              (32, 16, 0), (16, 16, 0), (16, 16, 0)]
+    fwd_flops = sum(2.0 * (V / 8 ** lv) * 27 * ci * co for ci, co, lv in layers)
+    stream = torch.cuda.current_stream()
+    t_f = _time(lambda: net.forward(n, x, y), 5, stream, torch)
+    t_fb = _time(lambda: net.loss_grad(n, x, t), 5, stream, torch)
+    pk = peaks().get("bf16_tflops")
+    return {"n": n, "cells": V, "forward_ms": t_f, "forward_backward_ms": t_fb,
+            "forward_tflops": fwd_flops / (t_f * 1e-3) / 1e12, "train_step_tflops": 3 * fwd_flops / (t_fb * 1e-3) / 1e12,
+            "bf16_peak_tflops_measured": pk}
+
+
+def run_guess(args, sdx, torch):
+    """Learned initial guess: train the network on solves at 64^3 (random boxes, contrast
+    1-1e4, Gaussian blobs), then solve unseen 128^3 layouts from zero and from the guess to the
+    same residual; times of the guess include the prediction."""
+    from paper_1604_07994_gb300 import guess, workloads as W
+    X, T, gen = guess.training_set(args.guess_samples, n=64)
+    net = sdx.Net(seed=11)
+    hist, t_train = guess.train(net, X, T, epochs=args.guess_epochs, batch=8, lr=2e-3)
+    evalp = [W.random_instance(128, 8, 90000 + k, 8, log10_contrast=(0.0, 4.0), forcing="blobs")
+             for k in range(args.guess_eval)]
+    steps = tuple(int(k) for k in args.guess_smooth.split(","))
+    ev = guess.evaluate(net, evalp, smooth_steps=steps)
+    out = {"training_set": gen, "epochs": args.guess_epochs, "train_s": t_train, "loss_first_last": [hist[0], hist[-1]],
+           "eval": ev, "iterations_zero_mean": float(np.mean([e["zero"]["iterations"] for e in ev]))}
+    z = sum(e["zero"]["seconds"] for e in ev)
+    for k in steps:
+        key = f"guess_s{k}"
+        out[f"iterations_{key}_mean"] = float(np.mean([e[key]["iterations"] for e in ev]))
+        out[f"wall_time_saved_frac_{key}"] = (z - sum(e[key]["seconds"] for e in ev)) / z
     return out
 
 

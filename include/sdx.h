@@ -314,7 +314,9 @@ int sdx_guess_features(sdx_hier_t h, const double* f_nodal, uint16_t* x, double*
                        void* stream);
 
 /* Training target from a solution (device SoA vector of the finest level): t[n^3][16] (FP32)
- * with the cell means of (u_x, u_y, u_z, p) / fscale in channels 0..3, zeros elsewhere. */
+ * with the cell means of 100 u_x, 100 u_y, 100 u_z and p - (mean of p over the nodes), all
+ * over fscale, in channels 0..3, zeros elsewhere (the factor 100 brings the velocities of the
+ * blob-forced problems to the size of the pressures).  Synchronises the stream. */
 int sdx_guess_target(sdx_hier_t h, const double* x_solution, double fscale, float* target,
                      void* stream);
 
@@ -324,6 +326,12 @@ int sdx_guess_target(sdx_hier_t h, const double* x_solution, double fscale, floa
  * last grid it saw (resizing synchronises the device). */
 int sdx_guess_predict(sdx_hier_t h, sdx_net_t net, const double* f_nodal, double* x0,
                       void* stream);
+
+/* Make a predicted iterate safe to start from: `steps` FP64 Uzawa smoothing steps on the
+ * finest level (as sdx_uzawa) with right-hand side b, then x is replaced by its
+ * residual-minimising multiple alpha x, alpha = (Kx, b) / (Kx, Kx), so that
+ * ||b - K x|| <= ||b|| always holds.  Asynchronous.  Not for batch-owned hierarchies. */
+int sdx_guess_refine(sdx_hier_t h, const double* b, double* x, int steps, void* stream);
 
 /* Number of CUDA kernels this library has launched in the process so far (all
  * hierarchies, all threads); used to count the kernels of a timed region. */

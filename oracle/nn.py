@@ -201,16 +201,25 @@ def features(cell_mu, f_nodal, n):
     return x, fscale
 
 
+VEL_SCALE = 100.0  # velocity channels are VEL_SCALE u / fscale, pressure (p - mean p) / fscale
+
+
 def target(x_nodes, fscale, n):
-    """Training target [n^3, 16]: cell means of the nodal solution (u_x, u_y, u_z, p) / fscale."""
+    """Training target [n^3, 16]: cell means of the nodal solution, channels 0..2 scaled to
+    VEL_SCALE u / fscale, channel 3 = (p - mean over nodes of p) / fscale (the pressure is
+    defined up to a constant without a traction face)."""
+    x = np.asarray(x_nodes).reshape(4, -1).copy()
+    x[3] -= x[3].mean()
     t = np.zeros((n ** 3, 16))
-    t[:, :4] = _corner_mean(np.asarray(x_nodes).reshape(4, -1), n) / fscale
+    t[:, :4] = _corner_mean(x, n) / fscale
+    t[:, :3] *= VEL_SCALE
     return t
 
 
 def to_nodes(y, fscale, n, constrained):
     """Initial guess on the nodes: mean of the prediction over the (1 to 8) cells around
-    each node, times fscale; constrained velocity components set to zero.  SoA [4 (n+1)^3]."""
+    each node, unscaled (velocity / VEL_SCALE, times fscale); constrained velocity components
+    set to zero.  SoA [4 (n+1)^3]."""
     g = y[:, :4].T.reshape(4, n, n, n)
     acc = np.zeros((4, n + 1, n + 1, n + 1))
     cnt = np.zeros((n + 1, n + 1, n + 1))
@@ -219,6 +228,15 @@ def to_nodes(y, fscale, n, constrained):
             for c in (0, 1):
                 acc[:, a:a + n, b:b + n, c:c + n] += g
                 cnt[a:a + n, b:b + n, c:c + n] += 1.0
-    out = (acc / cnt[None]).reshape(-1) * fscale
+    out = acc / cnt[None] * fscale
+    out[:3] /= VEL_SCALE
+    out = out.reshape(-1)
     out[np.asarray(constrained, dtype=bool)] = 0.0
     return out
+
+
+def line_search(K, b, x):
+    """The residual-minimising multiple of x: alpha x with alpha = (Kx, b) / (Kx, Kx)."""
+    y = K @ x
+    d = float(y @ y)
+    return x * (float(y @ b) / d if d > 0 else 0.0)

@@ -1,5 +1,6 @@
 // Device kernels: operator apply / residual, Uzawa smoother passes, transfers, right-hand
 // side, vector helpers and the dense coarse-grid solve.
+#include <algorithm>
 #include <atomic>
 #include <cstdio>
 #include <mutex>
@@ -340,6 +341,108 @@ __global__ void k_gj_init(double* aug, const double* a, int n) {
     aug[t] = c < n ? a[i * n + c] : (c - n == i ? 1.0 : 0.0);
 }
 
+// ------------------------------------------------------------------ cooperative smoothing
+// All nu Uzawa steps of one (small) level in ONE launch: the phases of the multi-kernel
+// smoother (special velocity rows of a colour; uniform nodes of that colour with the scatter of
+// the special rows; the two pressure colours) are separated by grid-wide barriers instead of
+// kernel boundaries.  Within a phase the same per-node bodies run, on the same values, so the
+// result is bit-identical to launch_uzawa.  The launch is cooperative (all blocks resident);
+// every barrier wait is bounded and a time-out sets *err and ends the kernel.
+constexpr int COOP_TPB = 256;
+constexpr long long BARRIER_LIMIT = 2000000000LL;  // clock cycles (about one second)
+
+__device__ __forceinline__ bool grid_sync(unsigned* bar, unsigned nblocks, int* err) {
+    __shared__ int fail;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        fail = 0;
+        volatile unsigned* gen = bar + 1;
+        const unsigned g = *gen;
+        __threadfence();
+        if (atomicAdd(bar, 1u) == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g) {
+                if (clock64() - t0 > BARRIER_LIMIT) {
+                    atomicExch(err, 1);
+                    fail = 1;
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        if (*(volatile int*)err) fail = 1;
+    }
+    __syncthreads();
+    return !fail;
+}
+
+template <typename T>
+struct CoopArgs {
+    LevelView<T> L;
+    T* x;
+    const T* b;
+    int steps;
+    const int* sv[2]; const T* cv[2]; int nv[2];   // special velocity rows per colour
+    const int* sp[2]; const T* cp[2]; int np[2];   // special pressure rows per colour
+    T* tmp;       // staged special velocity values (3 per row)
+    T* sym;       // strain form: new values of the uniform nodes (3 components)
+    unsigned* bar;  // [2]: arrivals, generation
+    int* err;
+};
+
+template <typename T, int FORM>
+__global__ void __launch_bounds__(COOP_TPB) k_uzawa_coop(CoopArgs<T> a) {
+    const LevelView<T> L = a.L;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long slots = colour_slots(L.n1);
+    const unsigned nb = gridDim.x;
+    T* x = a.x;
+    const T* b = a.b;
+    const T* g = b + 3 * L.nn;
+    for (int st = 0; st < a.steps; ++st) {
+        for (int q = 0; q < 3; ++q) {
+            const int c = q & 1;  // colours 0, 1, 0
+            const int nv = a.nv[c];
+            for (long long t = tid; t < nv; t += nth)
+                spec_row_slot<T, 1>(L, a.sv[c], nv, a.cv[c], x, a.tmp, b, (int)t);
+            if (!grid_sync(a.bar, nb, a.err)) return;
+            if (FORM == FORM_SYM) {
+                for (long long t = tid; t < slots; t += nth) {
+                    int i, j, k;
+                    if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, b, a.sym);
+                }
+                if (!grid_sync(a.bar, nb, a.err)) return;
+                for (long long t = tid; t < slots + nv; t += nth) {
+                    int i, j, k;
+                    if (t >= slots) vel_scatter_slot<T>(a.sv[c], (int)(t - slots), a.tmp, x, L.nn);
+                    else if (colour_slot(L.n1, c, t, i, j, k)) vel_copy_node<T>(L, i, j, k, a.sym, x);
+                }
+            } else {
+                for (long long t = tid; t < slots + nv; t += nth) {
+                    int i, j, k;
+                    if (t >= slots) vel_scatter_slot<T>(a.sv[c], (int)(t - slots), a.tmp, x, L.nn);
+                    else if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, b, nullptr);
+                }
+            }
+            if (!grid_sync(a.bar, nb, a.err)) return;
+        }
+        for (int c = 0; c < 2; ++c) {
+            const int np = a.np[c];
+            for (long long t = tid; t < slots + np; t += nth) {
+                int i, j, k;
+                if (t >= slots) spec_row_slot<T, 2>(L, a.sp[c], np, a.cp[c], x, nullptr, g, (int)(t - slots));
+                else if (colour_slot(L.n1, c, t, i, j, k)) pre_uniform_node<T>(L, i, j, k, x, g);
+            }
+            if (!grid_sync(a.bar, nb, a.err)) return;
+        }
+    }
+}
+
 }  // namespace
 
 // ===================================================================== launchers
@@ -482,6 +585,74 @@ void launch_uzawa(const Hier& H, int l, T* x, const T* b, cudaStream_t s) {
     }
     pressure_pass<T>(H, l, 0, x, b + 3 * L.nn, s);
     pressure_pass<T>(H, l, 1, x, b + 3 * L.nn, s);
+}
+
+template <typename T, int FORM>
+static bool uzawa_coop(const Hier& H, int l, T* x, const T* b, int steps, cudaStream_t s) {
+    const Level& L = H.lv[l];
+    static int sms = 0, resident[3][2] = {};
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    int& per_sm = resident[FORM][sizeof(T) == 8];
+    if (!per_sm && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_uzawa_coop<T, FORM>, COOP_TPB, 0) != cudaSuccess) {
+        cudaGetLastError();
+        per_sm = -1;
+    }
+    if (per_sm < 1) return false;
+    const long long slots = colour_slots(L.n + 1);
+    const long long work = slots + std::max(std::max(L.n_spec_vel[0], L.n_spec_vel[1]),
+                                            std::max(L.n_spec_pre[0], L.n_spec_pre[1]));
+    const long long want = (work + COOP_TPB - 1) / COOP_TPB;
+    const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(want, (long long)per_sm * sms));
+    CoopArgs<T> a;
+    a.L = view<T>(H, l);
+    a.x = x;
+    a.b = b;
+    a.steps = steps;
+    for (int c = 0; c < 2; ++c) {
+        a.sv[c] = L.spec_vel[c]; a.cv[c] = cf_vel<T>(L, c); a.nv[c] = L.n_spec_vel[c];
+        a.sp[c] = L.spec_pre[c]; a.cp[c] = cf_pre<T>(L, c); a.np[c] = L.n_spec_pre[c];
+    }
+    a.tmp = spec_scratch<T>(L);
+    a.sym = sym_scratch<T>(L);
+    a.bar = H.coop_bar;
+    a.err = H.coop_err;
+    if (cudaMemsetAsync(H.coop_bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return false;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(COOP_TPB);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_uzawa_coop<T, FORM>, a) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    count_launches(1);
+    return true;
+}
+
+// nu Uzawa steps on level l: one cooperative launch on levels up to coop_max_nodes nodes
+// (where the multi-kernel smoother is bound by launch latency), launch_uzawa otherwise.
+template <typename T>
+void launch_uzawa_steps(const Hier& H, int l, T* x, const T* b, int steps, cudaStream_t s) {
+    const Level& L = H.lv[l];
+    if (steps > 0 && H.use_coop && L.nn <= H.coop_max_nodes) {
+        bool ok = false;
+        switch (L.form) {
+            case FORM_SYM: ok = uzawa_coop<T, FORM_SYM>(H, l, x, b, steps, s); break;
+            case FORM_GRAD: ok = uzawa_coop<T, FORM_GRAD>(H, l, x, b, steps, s); break;
+            default: ok = uzawa_coop<T, FORM_TR>(H, l, x, b, steps, s);
+        }
+        if (ok) return;
+    }
+    for (int i = 0; i < steps; ++i) launch_uzawa<T>(H, l, x, b, s);
 }
 
 template <typename T>
@@ -661,6 +832,8 @@ template void launch_apply<double>(const Hier&, int, const double*, double*, con
 template void launch_apply<float>(const Hier&, int, const float*, float*, const float*, cudaStream_t);
 template void launch_uzawa<double>(const Hier&, int, double*, const double*, cudaStream_t);
 template void launch_uzawa<float>(const Hier&, int, float*, const float*, cudaStream_t);
+template void launch_uzawa_steps<double>(const Hier&, int, double*, const double*, int, cudaStream_t);
+template void launch_uzawa_steps<float>(const Hier&, int, float*, const float*, int, cudaStream_t);
 template void launch_smooth_pass<double>(const Hier&, int, int, int, double*, const double*, cudaStream_t);
 template void launch_smooth_pass<float>(const Hier&, int, int, int, float*, const float*, cudaStream_t);
 template void launch_restrict<double>(const Hier&, int, const double*, double*, cudaStream_t);

@@ -540,8 +540,14 @@ __global__ void k_features(LevelView<double> L, const double* __restrict__ f, co
     for (int c = 0; c < 16; ++c) x[v * 16 + c] = __float2bfloat16(o[c]);
 }
 
-// Training target: cell means of the nodal solution / fscale in channels 0..3.
-__global__ void k_target(LevelView<double> L, const double* __restrict__ xs, double fscale, float* __restrict__ t) {
+// Output channel c of the network is VEL_SCALE u_c / fscale (c < 3) or (p - mean p) / fscale
+// (c = 3): velocities of the blob-forced problems are about 1/100 of the pressures, and the
+// pressure without a traction face is defined up to a constant.
+constexpr double VEL_SCALE = 100.0;
+
+// Training target: cell means of the nodal solution, scaled as above, in channels 0..3.
+__global__ void k_target(LevelView<double> L, const double* __restrict__ xs, double fscale,
+                         const double* __restrict__ pmean, float* __restrict__ t) {
     const int n = L.n;
     const long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= (long long)n * n * n) return;
@@ -550,13 +556,28 @@ __global__ void k_target(LevelView<double> L, const double* __restrict__ xs, dou
         double s = 0;
         for (int q = 0; q < 8; ++q)
             s += xs[c * L.nn + (i + (q & 1)) + L.s1 * (j + ((q >> 1) & 1)) + L.s2 * (k + (q >> 2))];
-        t[v * 16 + c] = (float)(s * 0.125 / fscale);
+        s *= 0.125;
+        t[v * 16 + c] = (float)(c < 3 ? VEL_SCALE * s / fscale : (s - *pmean) / fscale);
     }
     for (int c = 4; c < 16; ++c) t[v * 16 + c] = 0.0f;
 }
 
-// Initial guess on the nodes: mean of the prediction over the cells around the node, times
-// fscale; constrained velocity components zero.
+// mean of count values -> *out (one block)
+__global__ void k_mean(const double* __restrict__ x, long long count, double* __restrict__ out) {
+    __shared__ double red[1024];
+    double s = 0;
+    for (long long t = threadIdx.x; t < count; t += blockDim.x) s += x[t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *out = red[0] / (double)count;
+}
+
+// Initial guess on the nodes: mean of the prediction over the cells around the node, unscaled
+// (velocity / VEL_SCALE, times fscale); constrained velocity components zero.
 __global__ void k_to_nodes(LevelView<double> L, const float* __restrict__ y, const double* __restrict__ fscale,
                            double* __restrict__ x0) {
     const long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -575,10 +596,17 @@ __global__ void k_to_nodes(LevelView<double> L, const float* __restrict__ y, con
     }
     const uint16_t inf = L.info[node];
     for (int c = 0; c < 4; ++c) {
-        double val = acc[c] / cnt * (*fscale);
+        double val = acc[c] / cnt * (*fscale) / (c < 3 ? VEL_SCALE : 1.0);
         if (c < 3 && (inf & (1u << c))) val = 0.0;
         x0[c * L.nn + node] = val;
     }
+}
+
+__global__ void k_negate(double* a) { *a = -*a; }
+
+// alpha = <y, b> / <y, y> with y = b - r = K x (the residual-minimising multiple of x)
+__global__ void k_line_alpha(const double* __restrict__ d, double* __restrict__ alpha) {
+    *alpha = d[1] > 0 ? d[0] / d[1] : 0.0;
 }
 
 // max |f| over the three nodal forcing components (1 if zero) -> *out
@@ -1066,10 +1094,16 @@ int sdx_guess_target(sdx_hier_t h, const double* xs, double fscale, float* t, vo
     Hier* H = reinterpret_cast<Hier*>(h);
     if (!H || !xs || !t || !(fscale > 0)) { set_error("invalid argument"); return SDX_EINVAL; }
     API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
     const LevelView<double> L = view<double>(*H, 0);
-    count_launches(1);
-    k_target<<<eblocks((long long)L.n * L.n * L.n), ETPB, 0, (cudaStream_t)stream>>>(L, xs, fscale, t);
-    return launched("sdx_guess_target");
+    double* pm = dalloc<double>(1);
+    count_launches(2);
+    k_mean<<<1, 1024, 0, s>>>(xs + 3 * L.nn, L.nn, pm);
+    k_target<<<eblocks((long long)L.n * L.n * L.n), ETPB, 0, s>>>(L, xs, fscale, pm, t);
+    const int rc = launched("sdx_guess_target");
+    CK(cudaStreamSynchronize(s));
+    cudaFree(pm);
+    return rc;
     API_END
 }
 
@@ -1088,6 +1122,27 @@ int sdx_guess_predict(sdx_hier_t h, sdx_net_t net, const double* f, double* x0, 
     count_launches(1);
     k_to_nodes<<<eblocks(L.nn), ETPB, 0, s>>>(L, N->y, N->fscale, x0);
     return launched("sdx_guess_predict");
+    API_END
+}
+
+int sdx_guess_refine(sdx_hier_t h, const double* b, double* x, int steps, void* stream) {
+    Hier* H = reinterpret_cast<Hier*>(h);
+    if (!H || !b || !x || steps < 0) { set_error("invalid argument"); return SDX_EINVAL; }
+    if (H->released) { set_error("this hierarchy belongs to a batch: use the sdx_batch_* calls"); return SDX_EINVAL; }
+    API_BEGIN
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long v4 = 4 * H->lv[0].nn;
+    for (int k = 0; k < steps; ++k) launch_uzawa<double>(*H, 0, x, b, s);
+    // y = K x = b - r;  alpha = <y, b> / <y, y>;  x *= alpha
+    launch_apply<double>(*H, 0, x, H->r0, b, s);
+    vec_axpy(H->r0, b, -1.0, v4, s);  // r0 = r - b = -y
+    vec_dot(*H, H->r0, b, v4, H->scal + 250, s);
+    vec_dot(*H, H->r0, H->r0, v4, H->scal + 251, s);
+    count_launches(2);
+    k_line_alpha<<<1, 1, 0, s>>>(H->scal + 250, H->scal + 252);
+    k_negate<<<1, 1, 0, s>>>(H->scal + 252);
+    vec_scale_dev(x, x, H->scal + 252, false, v4, s);
+    return launched("sdx_guess_refine");
     API_END
 }
 

@@ -300,7 +300,8 @@ void hier_free(Hier* H) {
             if (p) cudaFree(p);
     }
     void* ptrs[] = {H->mu_d, H->mu_f, H->coarse.free_idx, H->coarse.kinv, H->coarse.bc,
-                    H->coarse.xc, H->red_part, H->scal, H->r0, H->xh, H->bh, H->e};
+                    H->coarse.xc, H->red_part, H->scal, H->r0, H->xh, H->bh, H->e, H->coop_bar,
+                    H->coop_err};
     if (H->g64.exec) cudaGraphExecDestroy(H->g64.exec);
     if (H->g32.exec) cudaGraphExecDestroy(H->g32.exec);
     if (H->cap) cudaStreamDestroy(H->cap);
@@ -392,6 +393,13 @@ Hier* hier_create(const sdx_desc* d) {
         H->e = dalloc<double>(v4);
         const char* ng = std::getenv("SDX_NO_GRAPH");
         H->use_graph = !(ng && ng[0] == '1');
+        const char* nc = std::getenv("SDX_NO_COOP");
+        H->use_coop = !(nc && nc[0] == '1');
+        if (const char* cm = std::getenv("SDX_COOP_MAX_NODES")) H->coop_max_nodes = std::atoll(cm);
+        H->coop_bar = dalloc<unsigned>(2);
+        H->coop_err = dalloc<int>(1);
+        CK(cudaMemset(H->coop_bar, 0, 2 * sizeof(unsigned)));
+        CK(cudaMemset(H->coop_err, 0, sizeof(int)));
         build_coarse(*H);
         CK(cudaDeviceSynchronize());
     } catch (...) {
@@ -427,7 +435,7 @@ static void vcycle_rec(Hier& H, int l, T* x, const T* b, cudaStream_t s) {
     Level& L = H.lv[l];
     Level& Lc = H.lv[l + 1];
     const int nu = 3 + 2 * l;
-    for (int i = 0; i < nu; ++i) launch_uzawa<T>(H, l, x, b, s);
+    launch_uzawa_steps<T>(H, l, x, b, nu, s);
     T* r = Buf<T>::r(L);
     launch_apply<T>(H, l, x, r, b, s);
     launch_restrict<T>(H, l, r, Buf<T>::b(Lc), s);
@@ -435,7 +443,7 @@ static void vcycle_rec(Hier& H, int l, T* x, const T* b, cudaStream_t s) {
     if (l + 1 < last) vec_zero<T>(Buf<T>::x(Lc), 4 * Lc.nn, s);
     vcycle_rec<T>(H, l + 1, Buf<T>::x(Lc), Buf<T>::b(Lc), s);
     launch_prolong_add<T>(H, l, Buf<T>::x(Lc), x, s);
-    for (int i = 0; i < nu; ++i) launch_uzawa<T>(H, l, x, b, s);
+    launch_uzawa_steps<T>(H, l, x, b, nu, s);
 }
 
 // device scalar slots
@@ -443,11 +451,23 @@ enum { S_DOT = 0, S_NORM = 1, S_SCALE = 2, S_H = 8 };
 
 __global__ void k_sqrt(double* v) { *v = sqrt(*v); }
 
+// After a synchronisation: SDX_ETIMEOUT if a cooperative smoothing launch gave up a barrier.
+static void check_coop(Hier& H, cudaStream_t s) {
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, H.coop_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (e) {
+        CK(cudaMemsetAsync(H.coop_err, 0, sizeof(int), s));
+        set_error("a grid barrier of the cooperative smoother timed out");
+        throw Fail{SDX_ETIMEOUT};
+    }
+}
+
 static double norm_sync(Hier& H, const double* v, cudaStream_t s) {
     const long long v4 = 4 * H.lv[0].nn;
     vec_dot(H, v, v, v4, H.scal + S_NORM, s);
     CK(cudaMemcpyAsync(H.scal_host + S_NORM, H.scal + S_NORM, sizeof(double), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    check_coop(H, s);  // synchronises
     return std::sqrt(H.scal_host[S_NORM]);
 }
 
@@ -469,20 +489,33 @@ static void run_cycle(Hier& H, cudaStream_t s) {
     }
     if (!G.exec) {
         if (!H.cap) CK(cudaStreamCreateWithFlags(&H.cap, cudaStreamNonBlocking));
-        const long long before = launches_total();
-        CK(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
-        cudaGraph_t g = nullptr;
-        try {
-            zero_start_cycle<T>(H, H.cap);
-        } catch (...) {
-            cudaStreamEndCapture(H.cap, &g);
+        long long before = 0;
+        // a capture that cannot take the cooperative smoothing launches is redone without them
+        for (int attempt = 0; attempt < 2 && !G.exec; ++attempt) {
+            before = launches_total();
+            CK(cudaStreamBeginCapture(H.cap, cudaStreamCaptureModeThreadLocal));
+            cudaGraph_t g = nullptr;
+            try {
+                zero_start_cycle<T>(H, H.cap);
+            } catch (...) {
+                cudaStreamEndCapture(H.cap, &g);
+                if (g) cudaGraphDestroy(g);
+                throw;
+            }
+            cudaError_t e = cudaStreamEndCapture(H.cap, &g);
+            if (e == cudaSuccess) e = cudaGraphInstantiate(&G.exec, g, 0);
             if (g) cudaGraphDestroy(g);
-            throw;
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                G.exec = nullptr;
+                if (attempt == 0 && H.use_coop) {
+                    count_launches(-(launches_total() - before));
+                    H.use_coop = false;
+                    continue;
+                }
+                CK(e);
+            }
         }
-        CK(cudaStreamEndCapture(H.cap, &g));
-        const cudaError_t e = cudaGraphInstantiate(&G.exec, g, 0);
-        cudaGraphDestroy(g);
-        CK(e);
         G.kernels = launches_total() - before;
         count_launches(-G.kernels);  // captured, not executed
     }
@@ -597,7 +630,7 @@ static int solve(Hier& H, const double* b, double* x, double rtol, int maxit, in
             k_sqrt<<<1, 1, 0, s>>>(H.scal + S_H + j + 1);
             vec_scale_dev(H.V[j + 1], H.V[j + 1], H.scal + S_H + j + 1, true, v4, s);
             CK(cudaMemcpyAsync(H.scal_host + S_H, H.scal + S_H, sizeof(double) * (j + 2), cudaMemcpyDeviceToHost, s));
-            CK(cudaStreamSynchronize(s));
+            check_coop(H, s);  // synchronises
             S.iterations++;
             for (int i = 0; i <= j + 1; ++i) Hm[(size_t)i * m + j] = H.scal_host[S_H + i];
             for (int i = 0; i < j; ++i) {
@@ -745,7 +778,7 @@ int sdx_uzawa(sdx_hier_t h, int level, const double* b, double* x, void* stream)
     if (c) return c;
     if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
     API_BEGIN
-    launch_uzawa<double>(*H, level, x, b, (cudaStream_t)stream);
+    launch_uzawa_steps<double>(*H, level, x, b, 1, (cudaStream_t)stream);
     return launched("sdx_uzawa");
     API_END
 }

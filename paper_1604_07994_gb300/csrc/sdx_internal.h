@@ -24,6 +24,7 @@ constexpr uint8_t CELL_OUTSIDE = 255;  // id of the ghost cells around the domai
 
 constexpr double OMEGA = 0.3;  // pressure Gauss-Seidel relaxation (Sec. 5)
 constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle matrix (1.2 GB)
+constexpr long long COOP_MAX_NODES = 40000;  // default size limit of cooperative smoothing
 
 // Read-only view of one level as seen by kernels, for arithmetic type T.
 template <typename T>
@@ -116,6 +117,10 @@ struct Hier {
     cudaStream_t cap = nullptr;     // internal stream used only to capture the graphs
     bool use_graph = true;
     bool released = false;          // work vectors handed back (instance of a batch)
+    bool use_coop = true;           // cooperative smoothing launches on small levels
+    long long coop_max_nodes = COOP_MAX_NODES;
+    unsigned* coop_bar = nullptr;   // grid barrier state of the cooperative smoother [2]
+    int* coop_err = nullptr;        // set when a barrier wait of that smoother timed out
 };
 
 template <typename T>
@@ -126,6 +131,10 @@ template <typename T>
 void launch_apply(const Hier& H, int l, const T* x, T* y, const T* b, cudaStream_t s);
 template <typename T>
 void launch_uzawa(const Hier& H, int l, T* x, const T* b, cudaStream_t s);
+// `steps` Uzawa steps; levels of at most Hier::coop_max_nodes nodes run them in one
+// cooperative launch
+template <typename T>
+void launch_uzawa_steps(const Hier& H, int l, T* x, const T* b, int steps, cudaStream_t s);
 template <typename T>
 void launch_smooth_pass(const Hier& H, int l, int which, int colour, T* x, const T* b, cudaStream_t s);
 template <typename T>

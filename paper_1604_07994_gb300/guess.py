@@ -73,10 +73,12 @@ def train(net, X, T, epochs: int = 20, batch: int = 8, lr: float = 2e-3, seed: i
     return hist, time.perf_counter() - t0
 
 
-def evaluate(net, problems, rtol: float = 1e-8, coarse_form="sym", prec=sdx.PREC_FP64, restart: int = 30):
+def evaluate(net, problems, rtol: float = 1e-8, coarse_form="sym", prec=sdx.PREC_FP64, restart: int = 30,
+             smooth_steps=(4,)):
     """Solve every problem from zero and from the network's guess (same absolute tolerance).
-    Returns per-instance iterations, times (the guess time includes the prediction) and the
-    initial relative residuals."""
+    The guess is refined by `s` Uzawa smoothing steps and a residual-minimising scaling
+    (sdx_guess_refine) for every s in smooth_steps.  Returns per-instance iterations, times (a
+    guess's time includes prediction and refinement) and the initial relative residuals."""
     import torch
     out = []
     for p in problems:
@@ -89,16 +91,28 @@ def evaluate(net, problems, rtol: float = 1e-8, coarse_form="sym", prec=sdx.PREC
         net.predict(H, f, x)
         torch.cuda.synchronize()
         res = {}
-        for mode in ("zero", "guess"):
+        xstar = None
+        for mode in ["zero"] + [f"guess_s{k}" for k in smooth_steps]:
             x.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            if mode == "guess":
+            err0 = None
+            if mode != "zero":
                 net.predict(H, f, x)
+                sdx.sdx_guess_refine(H, b, x, int(mode[len("guess_s"):]))
+                torch.cuda.synchronize()
+                t_pred = time.perf_counter() - t0
+                d = x - xstar  # error of the start against the zero-start solution
+                d[3 * p.nodes:] -= d[3 * p.nodes:].mean()
+                err0 = float(d.norm() / xstar.norm())
+                t0 = time.perf_counter() - t_pred
             st = H.sdx_solve(b, x, rtol=rtol, maxit=400, outer=sdx.OUTER_FGMRES, restart=restart)
             torch.cuda.synchronize()
             res[mode] = {"iterations": st["iterations"], "seconds": time.perf_counter() - t0,
-                         "initial_rel_res": st["res0"] / st["bnorm"], "final_rel_res": st["res"] / st["bnorm"]}
+                         "initial_rel_res": st["res0"] / st["bnorm"], "final_rel_res": st["res"] / st["bnorm"],
+                         "initial_rel_error": 1.0 if mode == "zero" else err0}
+            if mode == "zero":
+                xstar = x.clone()
         out.append({"name": p.name, "n": p.n, "contrast": float(p.mu.max() / p.mu.min()), **res})
         H.close()
     return out

@@ -34,7 +34,7 @@ EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_co
             "sdx_batch_vcycle", "sdx_batch_solve", "sdx_net_param_count", "sdx_net_create",
             "sdx_net_destroy", "sdx_net_get_params", "sdx_net_set_params", "sdx_net_forward",
             "sdx_net_loss_grad", "sdx_net_train", "sdx_conv3", "sdx_conv3_wgrad", "sdx_guess_features",
-            "sdx_guess_target", "sdx_guess_predict", "sdx_last_error", "sdx_strerror")
+            "sdx_guess_target", "sdx_guess_predict", "sdx_guess_refine", "sdx_last_error", "sdx_strerror")
 
 
 class SdxError(RuntimeError):
@@ -109,6 +109,7 @@ def load() -> ctypes.CDLL:
         "sdx_guess_features": [P, P, P, ctypes.POINTER(D), P],
         "sdx_guess_target": [P, P, D, P, P],
         "sdx_guess_predict": [P, P, P, P, P],
+        "sdx_guess_refine": [P, P, P, I, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -419,6 +420,10 @@ def sdx_guess_features(hier: "Hierarchy", f_nodal, x_bf16, stream=None) -> float
     fs = ctypes.c_double()
     _check(load().sdx_guess_features(hier._h, _ptr(f_nodal), _ptr(x_bf16, 2), ctypes.byref(fs), _stream(stream)))
     return fs.value
+
+
+def sdx_guess_refine(hier: "Hierarchy", b, x, steps, stream=None):
+    _check(load().sdx_guess_refine(hier._h, _ptr(b), _ptr(x), int(steps), _stream(stream)))
 
 
 def sdx_guess_target(hier: "Hierarchy", x_solution, fscale, target_f32, stream=None):

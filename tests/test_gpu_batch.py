@@ -137,6 +137,14 @@ def test_batch_edge_cases(sdx):
     st1 = one.sdx_batch_solve([bs[1]], [x1], rtol=1e-10, maxit=100)
     assert st1[0]["iterations"] == st[1]["iterations"]
     assert np.array_equal(_host(x1), _host(xs[1]))  # instances do not influence each other
+    # a batch-owned hierarchy serves queries and the operator, not the solver calls
+    H = B.instance(1)
+    r = torch.empty_like(bs[1])
+    H.sdx_residual(0, bs[1], xs[1], r)
+    assert float(torch.linalg.norm(r)) <= 1e-10 * float(torch.linalg.norm(bs[1]))
+    with pytest.raises(sdx.SdxError) as e:
+        H.sdx_vcycle(bs[1], xs[1])
+    assert e.value.code == sdx.EINVAL
 
 
 def test_batch_benchmark_sizes_reach_tolerance(sdx):

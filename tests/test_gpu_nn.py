@@ -154,3 +154,24 @@ def test_solver_network_maps_match_oracle(sdx):
     net.forward(12, xb, y)
     x0ref = ON.to_nodes(y.cpu().numpy().astype(np.float64), fs, 12, con)
     assert np.abs(x0.cpu().numpy() - x0ref).max() <= 1e-6 * max(np.abs(x0ref).max(), 1e-30)
+
+
+def test_guess_refine_matches_oracle(sdx):
+    """sdx_guess_refine = Uzawa smoothing steps on the finest level, then the residual-
+    minimising multiple of the iterate; compared with the oracle's smoother and line search."""
+    from oracle.solvers import Level
+    p = W.random_instance(12, 3, 4, 3, forcing="blobs")
+    L = Level(p.n, p.cell_mu().ravel(), p.face, "tr")
+    b = L.disc.rhs(p.nodal_forcing())
+    H = sdx.Hierarchy.from_problem(p)
+    x0 = W.random_vector(12, 8).ravel() * 1e-3
+    x0[H.sdx_constraint_mask(0)] = 0.0
+    xd = torch.from_numpy(x0.copy()).cuda()
+    sdx.sdx_guess_refine(H, torch.from_numpy(b).cuda(), xd, 2)
+    xo = x0.copy()
+    for _ in range(2):
+        L.uzawa(xo, b)
+    xo = ON.line_search(L.K, b, xo)
+    got = xd.cpu().numpy()
+    assert np.linalg.norm(got - xo) <= 1e-10 * np.linalg.norm(xo)
+    assert np.linalg.norm(b - L.K @ got) <= np.linalg.norm(b)

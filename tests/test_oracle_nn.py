@@ -107,11 +107,26 @@ def test_node_cell_maps_reproduce_linear_fields():
     c = (np.arange(n) + 0.5) / n
     cz, cy, cx = np.meshgrid(c, c, c, indexing="ij")
     lin_c = (0.3 + 2.0 * cx - 1.5 * cy + 0.25 * cz).ravel()
-    assert np.allclose(cells[:, 0], lin_c / 2.0) and np.allclose(cells[:, 3], 3 * lin_c / 2.0)
+    assert np.allclose(cells[:, 0], N.VEL_SCALE * lin_c / 2.0)
+    # pressure: the node mean is removed first (cell means of a linear field keep that mean)
+    assert np.allclose(cells[:, 3], 3 * (lin_c - lin.mean()) / 2.0)
     back = N.to_nodes(cells, 2.0, n, np.zeros(4 * (n + 1) ** 3, dtype=bool)).reshape(4, n + 1, n + 1, n + 1)
     inner = (slice(None), slice(1, n), slice(1, n), slice(1, n))
-    assert np.allclose(back[inner], nodal.reshape(4, n + 1, n + 1, n + 1)[inner], atol=1e-13)
+    want = nodal.copy()
+    want[3] -= want[3].mean()
+    assert np.allclose(back[inner], want.reshape(4, n + 1, n + 1, n + 1)[inner], atol=1e-13)
     f = np.stack([lin, -lin, 0 * lin])
     feats, fs = N.features(np.full(n ** 3, 100.0), f, n)
     assert fs == np.abs(f).max() and np.allclose(feats[:, 0], 2.0) and np.all(feats[:, 4] == 1.0)
     assert np.allclose(feats[:, 1], lin_c / fs) and np.all(feats[:, 5:] == 0.0)
+
+
+def test_line_search_minimises_the_residual():
+    r = _rng(5)
+    K = r.standard_normal((6, 6)) + 6 * np.eye(6)
+    b = r.standard_normal(6)
+    x = r.standard_normal(6)
+    xs = N.line_search(K, b, x)
+    a = xs[0] / x[0]
+    res = lambda t: np.linalg.norm(b - t * (K @ x))
+    assert res(a) <= min(res(a - 1e-6), res(a + 1e-6)) and res(a) <= np.linalg.norm(b)
