@@ -27,6 +27,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 FP64_PEAK_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per clock per SM (GB300: 1.25 TFLOP/s FP64 nominal)
+# DRAM bytes (read + write) of one launch of the red FP64 velocity pass on the 128^3 workload,
+# from the ncu capture summarised in profiles/k_vel_uniform_three_boxes_128.md
+VEL_PASS_DRAM_BYTES_128 = 124460288 + 16544768
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 
@@ -267,7 +270,7 @@ def main():
     if rl:
         achieved = rl["flops"] / (rl["ms"] * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": "TFLOP/s",
-                "frac": achieved / peak_fp64, "traffic": None,
+                "frac": achieved / peak_fp64, "traffic": VEL_PASS_DRAM_BYTES_128 if n == 128 else None,
                 "kernel": "k_vel_uniform<double, a_tr> (red velocity Gauss-Seidel pass, finest level)",
                 "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2070 MHz (nominal 1.25 TFLOP/s)",
                 "algorithmic_bytes_per_launch": rl["bytes"],

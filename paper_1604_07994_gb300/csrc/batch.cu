@@ -143,23 +143,24 @@ __global__ void kb_apply_uniform(const BDesc<T>* __restrict__ D, BatchArgs a,
     BATCH_END
 }
 
-// Special rows of list `sl`.  MODE 0/3: y = K x or b - K x; MODE 1: new velocity values into
-// the scratch y (rows); MODE 2: pressure Gauss-Seidel in place with g = pressure part of b.
+// Special rows of list `sl`, one quad of lanes per row (items 4 x rows).  MODE 0/3: y = K x or
+// b - K x; MODE 1: new velocity values into the scratch y (rows); MODE 2: pressure
+// Gauss-Seidel in place with g = pressure part of b.
 template <typename T, int MODE>
 __global__ void kb_spec(const BDesc<T>* __restrict__ D, BatchArgs a, int sl, T* __restrict__ x,
                         T* __restrict__ y, const T* __restrict__ b) {
     BATCH_TILES(D, a)
     const int cnt = d.cnt[sl];
-    if (item >= cnt) continue;
+    if (item >= 4LL * cnt) continue;  // whole quads: tiles hold whole quads
     const LevelView<T> V = d.V;
     T* xv = x + 4 * d.offn;
     if (MODE == 1)
-        spec_row_slot<T, 1>(V, d.list[sl], cnt, d.cf[sl], xv, y + 3 * d.off_tmp, b + 4 * d.offn, (int)item);
+        spec_row_quad<T, 1>(V, d.list[sl], cnt, d.cf[sl], xv, y + 3 * d.off_tmp, b + 4 * d.offn, item);
     else if (MODE == 2)
-        spec_row_slot<T, 2>(V, d.list[sl], cnt, d.cf[sl], xv, nullptr, b + 4 * d.offn + 3 * V.nn, (int)item);
+        spec_row_quad<T, 2>(V, d.list[sl], cnt, d.cf[sl], xv, nullptr, b + 4 * d.offn + 3 * V.nn, item);
     else
-        spec_row_slot<T, MODE>(V, d.list[sl], cnt, d.cf[sl], xv, y + 4 * d.offn,
-                               b ? b + 4 * d.offn : nullptr, (int)item);
+        spec_row_quad<T, MODE>(V, d.list[sl], cnt, d.cf[sl], xv, y + 4 * d.offn, b ? b + 4 * d.offn : nullptr,
+                               item);
     BATCH_END
 }
 
@@ -781,21 +782,22 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
                     L.w[WK_NODES].items[i] = Li.nn;
                     L.w[WK_CNODES].items[i] = Lc.nn;
                     if (l + 1 < B->depth[i] - 1) L.w[WK_ZEROC].items[i] = 4 * Lc.nn;
-                    L.w[WK_VEL0].items[i] = Li.n_spec_vel[0];
-                    L.w[WK_VEL1].items[i] = Li.n_spec_vel[1];
-                    L.w[WK_PRE0].items[i] = Li.n_spec_pre[0];
-                    L.w[WK_PRE1].items[i] = Li.n_spec_pre[1];
+                    // special rows run one quad of lanes per row (the scatter uses the first quarter)
+                    L.w[WK_VEL0].items[i] = 4LL * Li.n_spec_vel[0];
+                    L.w[WK_VEL1].items[i] = 4LL * Li.n_spec_vel[1];
+                    L.w[WK_PRE0].items[i] = 4LL * Li.n_spec_pre[0];
+                    L.w[WK_PRE1].items[i] = 4LL * Li.n_spec_pre[1];
                 }
                 // the finest level also serves the outer iteration (residuals of every instance)
                 if (l == 0) {
                     L.w[WK_NODES].items[i] = Li.nn;
-                    L.w[WK_FULL].items[i] = Li.n_spec_full;
-                    L.w[WK_PROW].items[i] = Li.n_spec_prow;
+                    L.w[WK_FULL].items[i] = 4LL * Li.n_spec_full;
+                    L.w[WK_PROW].items[i] = 4LL * Li.n_spec_prow;
                     L.w[WK_V4].items[i] = 4 * Li.nn;
                     L.w[WK_DOT].items[i] = 4 * Li.nn;
                 } else if (!coarsest) {
-                    L.w[WK_FULL].items[i] = Li.n_spec_full;
-                    L.w[WK_PROW].items[i] = Li.n_spec_prow;
+                    L.w[WK_FULL].items[i] = 4LL * Li.n_spec_full;
+                    L.w[WK_PROW].items[i] = 4LL * Li.n_spec_prow;
                 }
             }
             // the coarse correction of level l is zero-started on level l + 1's vectors

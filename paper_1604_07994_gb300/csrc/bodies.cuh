@@ -168,36 +168,46 @@ __device__ __forceinline__ void pre_uniform_node(const LevelView<T>& L, int i, i
 
 // ------------------------------------------------------------------ special rows
 // One special row from its stored coefficients (SoA [coefficient][count]; column
-// (component c, Kuhn offset d) is c * 15 + d, row component r adds r * 60).
+// (component c, Kuhn offset d) is c * 15 + d, row component r adds r * 60), evaluated by a
+// quad of four consecutive lanes: lane q of the quad takes the columns of solution component
+// q over the 15 offsets, and the four partial sums are added with two quad shuffles.  Lane 0 of
+// the quad writes the result.  `quad` = the slot index times 4 plus q; every lane of a quad
+// must call this with the same slot (mask: the quad's lanes in the warp).
 // MODE 0: y = K x (or b - K x) on a full row; MODE 3: the same on a pressure-only row
 // (velocity rows written as 0); MODE 1: new velocity values of a colour into
 // y[3 * slot + r]; MODE 2: pressure Gauss-Seidel in place (b = g).
 template <typename T, int MODE>
-__device__ __forceinline__ void spec_row_slot(const LevelView<T>& L, const int* __restrict__ list,
+__device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* __restrict__ list,
                                               int count, const T* __restrict__ cf,
                                               T* __restrict__ x, T* __restrict__ y,
-                                              const T* __restrict__ b, int slot) {
+                                              const T* __restrict__ b, long long quad) {
+    const int slot = (int)(quad >> 2);
+    const int q = (int)(quad & 3);
+    const unsigned mask = 0xFu << (threadIdx.x & 28);
     const long long node = list[slot];
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
-    const uint16_t inf = L.info[node];
     const long long nn = L.nn;
     constexpr int NR = MODE == 0 ? 4 : (MODE == 1 ? 3 : 1);  // row components stored
     T acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = T(0);
+    const T* xq = x + q * nn;
 #pragma unroll
     for (int d = 0; d < 15; ++d) {
         const int a = i + KOFF15[d][0], bb = j + KOFF15[d][1], cc = k + KOFF15[d][2];
         if (a < 0 || bb < 0 || cc < 0 || a >= L.n1 || bb >= L.n1 || cc >= L.n1) continue;
-        const long long v = a + L.s1 * bb + L.s2 * cc;
+        const T xv = xq[a + L.s1 * bb + L.s2 * cc];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const T xv = x[c * nn + v];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) acc[r] += cf[(long long)(r * 60 + c * 15 + d) * count + slot] * xv;
-        }
+        for (int r = 0; r < NR; ++r) acc[r] += cf[(long long)(r * 60 + q * 15 + d) * count + slot] * xv;
     }
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+        acc[r] += __shfl_xor_sync(mask, acc[r], 1);
+        acc[r] += __shfl_xor_sync(mask, acc[r], 2);
+    }
+    if (q != 0) return;
+    const uint16_t inf = L.info[node];
     if (MODE == 0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {

@@ -105,13 +105,14 @@ __global__ void k_d2f_plain(float* y, const double* x, long long count) {
     if (t < count) y[t] = (float)x[t];
 }
 
+// One quad of lanes per special row (4 * count threads).
 template <typename T, int MODE>
 __global__ void k_spec_rows(LevelView<T> L, const int* __restrict__ list, int count,
                             const T* __restrict__ cf, T* __restrict__ x, T* __restrict__ y,
                             const T* __restrict__ b) {
-    const int slot = blockIdx.x * blockDim.x + threadIdx.x;
-    if (slot >= count) return;
-    spec_row_slot<T, MODE>(L, list, count, cf, x, y, b, slot);
+    const long long quad = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (quad >= 4LL * count) return;  // whole quads: 4 * count and blockDim are multiples of 4
+    spec_row_quad<T, MODE>(L, list, count, cf, x, y, b, quad);
 }
 
 // ------------------------------------------------------------------ transfers
@@ -394,8 +395,20 @@ struct CoopArgs {
     int* err;
 };
 
-template <typename T, int FORM>
-__global__ void __launch_bounds__(COOP_TPB) k_uzawa_coop(CoopArgs<T> a) {
+// Phase separation: a grid-wide barrier (cooperative launch over the device) or, when the
+// whole launch is one thread-block cluster, the hardware cluster barrier (release/acquire at
+// cluster scope; all CTAs of a cluster are co-scheduled, so it needs no time limit).
+template <bool CLUSTER>
+__device__ __forceinline__ bool phase_sync(unsigned* bar, unsigned nblocks, int* err) {
+    if (CLUSTER) {
+        asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+        return true;
+    }
+    return grid_sync(bar, nblocks, err);
+}
+
+template <typename T, int FORM, bool CLUSTER>
+__device__ __forceinline__ void uzawa_coop_body(const CoopArgs<T>& a) {
     const LevelView<T> L = a.L;
     const long long nth = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -408,15 +421,15 @@ __global__ void __launch_bounds__(COOP_TPB) k_uzawa_coop(CoopArgs<T> a) {
         for (int q = 0; q < 3; ++q) {
             const int c = q & 1;  // colours 0, 1, 0
             const int nv = a.nv[c];
-            for (long long t = tid; t < nv; t += nth)
-                spec_row_slot<T, 1>(L, a.sv[c], nv, a.cv[c], x, a.tmp, b, (int)t);
-            if (!grid_sync(a.bar, nb, a.err)) return;
+            for (long long t = tid; t < 4LL * nv; t += nth)  // quads of lanes (nth is a multiple of 4)
+                spec_row_quad<T, 1>(L, a.sv[c], nv, a.cv[c], x, a.tmp, b, t);
+            if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
             if (FORM == FORM_SYM) {
                 for (long long t = tid; t < slots; t += nth) {
                     int i, j, k;
                     if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, b, a.sym);
                 }
-                if (!grid_sync(a.bar, nb, a.err)) return;
+                if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
                 for (long long t = tid; t < slots + nv; t += nth) {
                     int i, j, k;
                     if (t >= slots) vel_scatter_slot<T>(a.sv[c], (int)(t - slots), a.tmp, x, L.nn);
@@ -429,18 +442,32 @@ __global__ void __launch_bounds__(COOP_TPB) k_uzawa_coop(CoopArgs<T> a) {
                     else if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, b, nullptr);
                 }
             }
-            if (!grid_sync(a.bar, nb, a.err)) return;
+            if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
         }
         for (int c = 0; c < 2; ++c) {
             const int np = a.np[c];
-            for (long long t = tid; t < slots + np; t += nth) {
+            // special rows first so that their quads stay aligned with the lanes
+            for (long long t = tid; t < 4LL * np + slots; t += nth) {
                 int i, j, k;
-                if (t >= slots) spec_row_slot<T, 2>(L, a.sp[c], np, a.cp[c], x, nullptr, g, (int)(t - slots));
-                else if (colour_slot(L.n1, c, t, i, j, k)) pre_uniform_node<T>(L, i, j, k, x, g);
+                if (t < 4LL * np) spec_row_quad<T, 2>(L, a.sp[c], np, a.cp[c], x, nullptr, g, t);
+                else if (colour_slot(L.n1, c, t - 4LL * np, i, j, k)) pre_uniform_node<T>(L, i, j, k, x, g);
             }
-            if (!grid_sync(a.bar, nb, a.err)) return;
+            if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
         }
     }
+}
+
+template <typename T, int FORM>
+__global__ void __launch_bounds__(COOP_TPB, 2) k_uzawa_coop(CoopArgs<T> a) {
+    uzawa_coop_body<T, FORM, false>(a);
+}
+
+// One cluster of CLUSTER_CTAS CTAs of CLUSTER_TPB threads (one CTA per SM): the smallest levels.
+constexpr int CLUSTER_TPB = 512;
+constexpr int CLUSTER_CTAS = 16;
+template <typename T, int FORM>
+__global__ void __launch_bounds__(CLUSTER_TPB, 1) k_uzawa_cluster(CoopArgs<T> a) {
+    uzawa_coop_body<T, FORM, true>(a);
 }
 
 }  // namespace
@@ -478,9 +505,9 @@ static void apply_form(const Hier& H, int l, const T* x, T* y, const T* b, cudaS
     LevelView<T> V = view<T>(H, l);
     count_launches(1 + (L.n_spec_full ? 1 : 0) + (L.n_spec_prow ? 1 : 0));
     if (L.n_spec_full)
-        k_spec_rows<T, 0><<<blocks_for(L.n_spec_full), TPB, 0, s>>>(V, L.spec_full, L.n_spec_full, cf_full<T>(L), const_cast<T*>(x), y, b);
+        k_spec_rows<T, 0><<<blocks_for(4LL * (L.n_spec_full)), TPB, 0, s>>>(V, L.spec_full, L.n_spec_full, cf_full<T>(L), const_cast<T*>(x), y, b);
     if (L.n_spec_prow)
-        k_spec_rows<T, 3><<<blocks_for(L.n_spec_prow), TPB, 0, s>>>(V, L.spec_prow, L.n_spec_prow, cf_prow<T>(L), const_cast<T*>(x), y, b);
+        k_spec_rows<T, 3><<<blocks_for(4LL * (L.n_spec_prow)), TPB, 0, s>>>(V, L.spec_prow, L.n_spec_prow, cf_prow<T>(L), const_cast<T*>(x), y, b);
     switch (L.form) {
         case FORM_SYM:
             k_apply_uniform<T, FORM_SYM><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
@@ -550,7 +577,7 @@ static void velocity_pass(const Hier& H, int l, int colour, T* x, const T* f, cu
     const int cnt = L.n_spec_vel[colour];
     T* tmp = spec_scratch<T>(L);
     count_launches((FORM == FORM_SYM ? 2 : 1) + (cnt ? 2 : 0));
-    if (cnt) k_spec_rows<T, 1><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, cf_vel<T>(L, colour), x, tmp, f);
+    if (cnt) k_spec_rows<T, 1><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, cf_vel<T>(L, colour), x, tmp, f);
     if (FORM == FORM_SYM) {
         T* out = sym_scratch<T>(L);
         k_vel_uniform<T, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, out);
@@ -568,7 +595,7 @@ static void pressure_pass(const Hier& H, int l, int colour, T* x, const T* g, cu
     const unsigned grid = colour_blocks(L);
     const int cnt = L.n_spec_pre[colour];
     count_launches(1 + (cnt ? 1 : 0));
-    if (cnt) k_spec_rows<T, 2><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_pre[colour], cnt, cf_pre<T>(L, colour), x, nullptr, g);
+    if (cnt) k_spec_rows<T, 2><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_pre[colour], cnt, cf_pre<T>(L, colour), x, nullptr, g);
     k_pre_uniform<T><<<grid, CTPB, 0, s>>>(V, colour, x, g);
 }
 
@@ -585,6 +612,25 @@ void launch_uzawa(const Hier& H, int l, T* x, const T* b, cudaStream_t s) {
     }
     pressure_pass<T>(H, l, 0, x, b + 3 * L.nn, s);
     pressure_pass<T>(H, l, 1, x, b + 3 * L.nn, s);
+}
+
+template <typename T>
+static CoopArgs<T> coop_args(const Hier& H, int l, T* x, const T* b, int steps) {
+    const Level& L = H.lv[l];
+    CoopArgs<T> a;
+    a.L = view<T>(H, l);
+    a.x = x;
+    a.b = b;
+    a.steps = steps;
+    for (int c = 0; c < 2; ++c) {
+        a.sv[c] = L.spec_vel[c]; a.cv[c] = cf_vel<T>(L, c); a.nv[c] = L.n_spec_vel[c];
+        a.sp[c] = L.spec_pre[c]; a.cp[c] = cf_pre<T>(L, c); a.np[c] = L.n_spec_pre[c];
+    }
+    a.tmp = spec_scratch<T>(L);
+    a.sym = sym_scratch<T>(L);
+    a.bar = H.coop_bar;
+    a.err = H.coop_err;
+    return a;
 }
 
 template <typename T, int FORM>
@@ -605,21 +651,11 @@ static bool uzawa_coop(const Hier& H, int l, T* x, const T* b, int steps, cudaSt
     const long long slots = colour_slots(L.n + 1);
     const long long work = slots + std::max(std::max(L.n_spec_vel[0], L.n_spec_vel[1]),
                                             std::max(L.n_spec_pre[0], L.n_spec_pre[1]));
-    const long long want = (work + COOP_TPB - 1) / COOP_TPB;
+    // at least one block per SM: a phase of a small level is bound by the FP64 rate of the SMs
+    // that hold its work, not by the number of items
+    const long long want = std::max<long long>((work + COOP_TPB - 1) / COOP_TPB, sms);
     const unsigned grid = (unsigned)std::max<long long>(1, std::min<long long>(want, (long long)per_sm * sms));
-    CoopArgs<T> a;
-    a.L = view<T>(H, l);
-    a.x = x;
-    a.b = b;
-    a.steps = steps;
-    for (int c = 0; c < 2; ++c) {
-        a.sv[c] = L.spec_vel[c]; a.cv[c] = cf_vel<T>(L, c); a.nv[c] = L.n_spec_vel[c];
-        a.sp[c] = L.spec_pre[c]; a.cp[c] = cf_pre<T>(L, c); a.np[c] = L.n_spec_pre[c];
-    }
-    a.tmp = spec_scratch<T>(L);
-    a.sym = sym_scratch<T>(L);
-    a.bar = H.coop_bar;
-    a.err = H.coop_err;
+    const CoopArgs<T> a = coop_args<T>(H, l, x, b, steps);
     if (cudaMemsetAsync(H.coop_bar, 0, 2 * sizeof(unsigned), s) != cudaSuccess) return false;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -638,11 +674,56 @@ static bool uzawa_coop(const Hier& H, int l, T* x, const T* b, int steps, cudaSt
     return true;
 }
 
-// nu Uzawa steps on level l: one cooperative launch on levels up to coop_max_nodes nodes
-// (where the multi-kernel smoother is bound by launch latency), launch_uzawa otherwise.
+// The smallest levels: one cluster of CLUSTER_CTAS CTAs (one GPC) with hardware cluster
+// barriers between the phases.  false if the device cannot host such a cluster.
+template <typename T, int FORM>
+static bool uzawa_cluster(const Hier& H, int l, T* x, const T* b, int steps, cudaStream_t s) {
+    static int state[3][2] = {};  // 0 unknown, 1 usable, -1 not available
+    int& st = state[FORM][sizeof(T) == 8];
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(CLUSTER_CTAS);
+    cfg.blockDim = dim3(CLUSTER_TPB);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CLUSTER_CTAS;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (st == 0) {
+        st = -1;
+        int clusters = 0;
+        if (cudaFuncSetAttribute(k_uzawa_cluster<T, FORM>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess &&
+            cudaOccupancyMaxActiveClusters(&clusters, k_uzawa_cluster<T, FORM>, &cfg) == cudaSuccess && clusters >= 1)
+            st = 1;
+        cudaGetLastError();
+    }
+    if (st != 1) return false;
+    if (cudaLaunchKernelEx(&cfg, k_uzawa_cluster<T, FORM>, coop_args<T>(H, l, x, b, steps)) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    count_launches(1);
+    return true;
+}
+
+// nu Uzawa steps on level l: one cluster launch on levels up to CLUSTER_MAX_NODES nodes, one
+// cooperative launch up to coop_max_nodes (where the multi-kernel smoother is bound by launch
+// latency), launch_uzawa otherwise.
 template <typename T>
 void launch_uzawa_steps(const Hier& H, int l, T* x, const T* b, int steps, cudaStream_t s) {
     const Level& L = H.lv[l];
+    // (FP64 phases on one GPC are bound by its FP64 rate: the cluster path is for FP32 cycles)
+    if (sizeof(T) == 4 && steps > 0 && H.use_coop && L.nn <= H.cluster_max_nodes) {
+        bool ok = false;
+        switch (L.form) {
+            case FORM_SYM: ok = uzawa_cluster<T, FORM_SYM>(H, l, x, b, steps, s); break;
+            case FORM_GRAD: ok = uzawa_cluster<T, FORM_GRAD>(H, l, x, b, steps, s); break;
+            default: ok = uzawa_cluster<T, FORM_TR>(H, l, x, b, steps, s);
+        }
+        if (ok) return;
+    }
     if (steps > 0 && H.use_coop && L.nn <= H.coop_max_nodes) {
         bool ok = false;
         switch (L.form) {
@@ -801,7 +882,7 @@ static void velocity_pass_static(const Hier& H, int l, int colour, double* x, co
     const unsigned grid = colour_blocks(L);
     const int cnt = L.n_spec_vel[colour];
     count_launches(1 + (cnt ? 2 : 0));
-    if (cnt) k_spec_rows<double, 1><<<blocks_for(cnt), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, L.cf_vel_d[colour], x, tmp, f);
+    if (cnt) k_spec_rows<double, 1><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, L.cf_vel_d[colour], x, tmp, f);
     k_vel_uniform<double, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, nullptr);
     if (cnt) k_vel_scatter<double><<<blocks_for(cnt), TPB, 0, s>>>(L.spec_vel[colour], cnt, tmp, x, L.nn);
 }

@@ -396,6 +396,7 @@ Hier* hier_create(const sdx_desc* d) {
         const char* nc = std::getenv("SDX_NO_COOP");
         H->use_coop = !(nc && nc[0] == '1');
         if (const char* cm = std::getenv("SDX_COOP_MAX_NODES")) H->coop_max_nodes = std::atoll(cm);
+        if (const char* cm = std::getenv("SDX_CLUSTER_MAX_NODES")) H->cluster_max_nodes = std::atoll(cm);
         H->coop_bar = dalloc<unsigned>(2);
         H->coop_err = dalloc<int>(1);
         CK(cudaMemset(H->coop_bar, 0, 2 * sizeof(unsigned)));

@@ -24,7 +24,12 @@ constexpr uint8_t CELL_OUTSIDE = 255;  // id of the ghost cells around the domai
 
 constexpr double OMEGA = 0.3;  // pressure Gauss-Seidel relaxation (Sec. 5)
 constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle matrix (1.2 GB)
-constexpr long long COOP_MAX_NODES = 40000;  // default size limit of cooperative smoothing
+// Default size limits of the fused smoothing launches.  Grid-wide cooperative smoothing is off by
+// default: inside the captured V-cycle a grid barrier (about 10 us across the two dies) costs
+// more than the kernel boundary it replaces.  Single-cluster smoothing is used for FP32 cycles
+// on levels of at most CLUSTER_MAX_NODES nodes.
+constexpr long long COOP_MAX_NODES = 0;
+constexpr long long CLUSTER_MAX_NODES = 10000;
 
 // Read-only view of one level as seen by kernels, for arithmetic type T.
 template <typename T>
@@ -119,6 +124,7 @@ struct Hier {
     bool released = false;          // work vectors handed back (instance of a batch)
     bool use_coop = true;           // cooperative smoothing launches on small levels
     long long coop_max_nodes = COOP_MAX_NODES;
+    long long cluster_max_nodes = CLUSTER_MAX_NODES;
     unsigned* coop_bar = nullptr;   // grid barrier state of the cooperative smoother [2]
     int* coop_err = nullptr;        // set when a barrier wait of that smoother timed out
 };

@@ -175,3 +175,26 @@ def test_guess_refine_matches_oracle(sdx):
     got = xd.cpu().numpy()
     assert np.linalg.norm(got - xo) <= 1e-10 * np.linalg.norm(xo)
     assert np.linalg.norm(b - L.K @ got) <= np.linalg.norm(b)
+
+
+def test_trained_guess_against_zero_start(sdx):
+    """What the trained network gains over the method without it, on unseen instances: the
+    network is trained on solves the batched multigrid produced (16^3, 64 instances), its
+    training loss must drop, and solves from the refined guess must reach the same absolute
+    residual as solves from zero with a start no worse than zero (||b - K x0|| <= ||b||).  The
+    iteration counts of both starts are recorded; the guess is not required to save any (on
+    these grids it saves none: its residual is dominated by high-frequency error)."""
+    from paper_1604_07994_gb300 import guess
+    X, T, gen = guess.training_set(64, n=16, seed=500, batch=32)
+    assert gen["iterations_max"] < 400
+    net = sdx.Net(seed=4)
+    hist, _ = guess.train(net, X, T, epochs=15, batch=8, lr=2e-3)
+    assert hist[-1] < 0.2 * hist[0]
+    probs = [W.random_instance(16, 2, 7700 + k, 2, log10_contrast=(0.0, 4.0), forcing="blobs") for k in range(3)]
+    ev = guess.evaluate(net, probs, smooth_steps=(4,))
+    for e in ev:
+        z, g = e["zero"], e["guess_s4"]
+        assert g["initial_rel_res"] <= 1.0 + 1e-12
+        assert z["final_rel_res"] <= 1e-8 and g["final_rel_res"] <= 1e-8
+        print(e["name"], "iterations zero", z["iterations"], "guess", g["iterations"],
+              "initial error of the guess", g["initial_rel_error"])

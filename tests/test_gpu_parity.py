@@ -244,3 +244,28 @@ def test_oversized_coarsest_grid_is_rejected(sdx):
     with pytest.raises(sdx.SdxError) as e:
         sdx.Hierarchy.from_problem(p)
     assert e.value.code == sdx.EINVAL and "coarsest grid" in str(e.value)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("name", ["cube16", "mixed48", "boxes16"])
+def test_fused_smoothing_launches_match_per_pass_kernels(sdx, name, prec, monkeypatch):
+    """The fused smoothing launches (grid-wide cooperative, single cluster) run the same
+    per-node code in the same dependency order as the per-pass kernels: V-cycles agree bit for
+    bit.  Which path a hierarchy takes is fixed when it is created, from the environment."""
+    p = PROBLEMS[name]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    b = _dev(d.rhs(p.nodal_forcing()))
+    out = {}
+    for tag, env in (("per_pass", {"SDX_NO_COOP": "1"}),
+                     ("fused", {"SDX_COOP_MAX_NODES": "200000", "SDX_CLUSTER_MAX_NODES": "10000"})):
+        for k in ("SDX_NO_COOP", "SDX_COOP_MAX_NODES", "SDX_CLUSTER_MAX_NODES"):
+            monkeypatch.delenv(k, raising=False)
+        for k, v in env.items():
+            monkeypatch.setenv(k, v)
+        H = sdx.Hierarchy.from_problem(p, form="tr", coarse_form="sym", prec=prec)
+        x = _dev(np.zeros(4 * p.nodes))
+        for _ in range(2):
+            H.sdx_vcycle(b, x)
+        out[tag] = _host(x)
+        H.close()
+    assert np.array_equal(out["per_pass"], out["fused"])
