@@ -64,6 +64,23 @@ def parse():
     return ap.parse_args()
 
 
+def job_time_ms(ms_local, device):
+    """The job's time per step: the maximum over ranks (replicas run independent solves; the
+    job is as slow as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return ms_local
+    t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(free_per_rank, world_size, ms):
+    """Whole-job throughput in GDoF/s: every rank solves its own problem of free_per_rank DoF."""
+    return world_size * free_per_rank / (ms * 1e-3) / 1e9
+
+
 def dist_env():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -246,12 +263,8 @@ def main():
     barrier()
     launches = sdx.sdx_kernel_launches() - l0
     clk = clocks.stop()
-    ms = e0.elapsed_time(e1) / args.steps
-    if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = ws * free / (ms * 1e-3) / 1e9
+    ms = job_time_ms(e0.elapsed_time(e1) / args.steps, dev)
+    value = job_value(free, ws, ms)
     final_res = st["res"] / st["bnorm"]
 
     extra = {}

@@ -68,6 +68,8 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
     const long long nn = L.nn;
     Nb15<T> P;
     load_nb15(x + 3 * nn, node, L, P);
+    T hbt[3];
+    bt3(P, h2, hbt);
     T bu = 0;
     Nb15<T> U[3];
 #pragma unroll
@@ -84,7 +86,7 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
             for (int ii = 0; ii < 3; ++ii)
                 if (ii != jj) lap += xstencil(U[ii], ii, jj);
         }
-        const T row = muh * lap - h2 * bstencil(P, jj);
+        const T row = muh * lap - hbt[jj];
         y[jj * nn + node] = b ? b[jj * nn + node] - row : row;
     }
     const T cp = tauh * (T(6) * P.c - (P.S(EX) + P.S(EY) + P.S(EZ)));
@@ -109,6 +111,8 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
     const long long nn = L.nn;
     Nb15<T> P;
     load_nb15(x + 3 * nn, node, L, P);
+    T hbt[3];
+    bt3(P, h2, hbt);
     if (FORM == FORM_SYM) {
         Nb15<T> U[3];
 #pragma unroll
@@ -119,7 +123,7 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
                 if (ii != jj) lap += xstencil(U[ii], ii, jj);
-            const T row = muh * lap - h2 * bstencil(P, jj);
+            const T row = muh * lap - hbt[jj];
             out[jj * nn + node] = U[jj].c + (f[jj * nn + node] - row) * inv;
         }
     } else {
@@ -127,7 +131,7 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
         for (int jj = 0; jj < 3; ++jj) {
             T* u = x + jj * nn;
             const T c = u[node];
-            const T row = muh * lap7(u, node, L, c) - h2 * bstencil(P, jj);
+            const T row = muh * lap7(u, node, L, c) - hbt[jj];
             u[node] = c + (f[jj * nn + node] - row) * inv;
         }
     }

@@ -83,6 +83,23 @@ __device__ __forceinline__ T bstencil(const Nb15<T>& v, int ax) {
     return T(0.25) * v.A(ax) + bsum_axis(v, ax) * T(1.0 / 12.0);
 }
 
+// h^2 * bstencil(P, j) for the three components at once, sharing the seven differences
+// A_d(P): with S = A_xy + A_xz + A_yz + A_xyz, Q = A_x + A_y + A_z and D = S - Q,
+//     bsum_axis(P, j) = D + A_j - 2 A_pair(j),   pair(x) = yz, pair(y) = xz, pair(z) = xy,
+// so bstencil(P, j) = A_j / 3 - A_pair(j) / 6 + D / 12.
+template <typename T>
+__device__ __forceinline__ void bt3(const Nb15<T>& P, T h2, T out[3]) {
+    T A[7];
+#pragma unroll
+    for (int d = 0; d < 7; ++d) A[d] = P.A(d);
+    const T D = (A[EXY] + A[EXZ] + A[EYZ] + A[EXYZ]) - (A[EX] + A[EY] + A[EZ]);
+    const T c1 = h2 * T(1.0 / 3.0), c2 = h2 * T(-1.0 / 6.0);
+    const T Dh = D * (h2 * T(1.0 / 12.0));
+    out[0] = c1 * A[EX] + (c2 * A[EYZ] + Dh);
+    out[1] = c1 * A[EY] + (c2 * A[EXZ] + Dh);
+    out[2] = c1 * A[EZ] + (c2 * A[EXY] + Dh);
+}
+
 __device__ __forceinline__ int pair_dir(int i, int j) {
     // direction e_i + e_j for i != j
     int s = i + j;
