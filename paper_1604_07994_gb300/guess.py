@@ -5,7 +5,7 @@ data (sdx_batch_solve), the feature and target maps (sdx_guess_features / sdx_gu
 the network's tensor-core forward and backward passes and Adam (sdx_net_train), and the
 prediction (sdx_guess_predict).  This module only loops over instances and moves pointers.
 
-The zero-guess multigrid stays the judge: a solve from the predicted iterate runs to the same
+The zero-guess multigrid stays the reference: a solve from the predicted iterate runs to the same
 absolute residual ||b - K x|| <= rtol ||b|| as the solve from zero, so the network can only
 save iterations, never accuracy.
 """
