@@ -31,38 +31,52 @@ __global__ void k_apply_uniform(LevelView<T> L, const T* __restrict__ x, T* __re
 }
 
 // ------------------------------------------------------------------ smoother passes
-// Colour-pass kernels: one thread per colour slot (see colour_slot).
+// Colour-pass kernels: one thread per colour slot (see colour_slot), plus one thread per staged
+// special row of the colour.  The uniform rows of a_tr / the gradient form read only velocities
+// of the other colour (7-point Laplacian) and the pressure, so the scatter of the colour's
+// staged special rows can run in the same launch: the two groups write disjoint nodes.
 template <typename T, int FORM>
 __global__ void k_vel_uniform(LevelView<T> L, int colour, T* __restrict__ x,
-                              const T* __restrict__ f, T* __restrict__ out) {
+                              const T* __restrict__ f, T* __restrict__ out,
+                              const int* __restrict__ list, int cnt, const T* __restrict__ tmp) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long slots = colour_slots(L.n1);
     int i, j, k;
-    if (!colour_slot(L.n1, colour, (long long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
-    vel_uniform_node<T, FORM>(L, i, j, k, x, f, out);
+    if (t < slots) {
+        if (colour_slot(L.n1, colour, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, f, out);
+    } else if (t < slots + cnt) {
+        vel_scatter_slot<T>(list, (int)(t - slots), tmp, x, L.nn);
+    }
 }
 
-template <typename T>
-__global__ void k_vel_scatter(const int* __restrict__ list, int count, const T* __restrict__ tmp,
-                              T* __restrict__ x, long long nn) {
-    int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= count) return;
-    vel_scatter_slot<T>(list, t, tmp, x, nn);
-}
-
-// strain form: copy the colour's new uniform-node values back
+// Strain form (whose uniform rows read same-colour velocities, so the new values were written
+// to `src`): copy the colour's uniform values back and scatter its staged special rows.
 template <typename T>
 __global__ void k_vel_copy_colour(LevelView<T> L, int colour, const T* __restrict__ src,
-                                  T* __restrict__ x) {
+                                  T* __restrict__ x, const int* __restrict__ list, int cnt,
+                                  const T* __restrict__ tmp) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long slots = colour_slots(L.n1);
     int i, j, k;
-    if (!colour_slot(L.n1, colour, (long long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
-    vel_copy_node<T>(L, i, j, k, src, x);
+    if (t < slots) {
+        if (colour_slot(L.n1, colour, t, i, j, k)) vel_copy_node<T>(L, i, j, k, src, x);
+    } else if (t < slots + cnt) {
+        vel_scatter_slot<T>(list, (int)(t - slots), tmp, x, L.nn);
+    }
 }
 
+// Pressure pass of a colour in one launch: the special rows (one quad of lanes each, first so
+// that quads stay aligned) and the uniform nodes.  Both update p of this colour in place and read
+// p only at the other colour (the special rows' same-colour couplings of C are exactly zero on
+// the Kuhn mesh) and u, which this pass does not write.
 template <typename T>
 __global__ void k_pre_uniform(LevelView<T> L, int colour, T* __restrict__ x,
-                              const T* __restrict__ g) {
+                              const T* __restrict__ g, const int* __restrict__ list, int cnt,
+                              const T* __restrict__ cf) {
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i, j, k;
-    if (!colour_slot(L.n1, colour, (long long)blockIdx.x * blockDim.x + threadIdx.x, i, j, k)) return;
-    pre_uniform_node<T>(L, i, j, k, x, g);
+    if (t < 4LL * cnt) spec_row_quad<T, 2>(L, list, cnt, cf, x, nullptr, g, t);
+    else if (colour_slot(L.n1, colour, t - 4LL * cnt, i, j, k)) pre_uniform_node<T>(L, i, j, k, x, g);
 }
 
 // ------------------------------------------------------------------ special rows as stencils
@@ -473,10 +487,6 @@ __global__ void __launch_bounds__(CLUSTER_TPB, 1) k_uzawa_cluster(CoopArgs<T> a)
 }  // namespace
 
 // ===================================================================== launchers
-static unsigned colour_blocks(const Level& L) {
-    const long long slots = (long long)((L.n + 2) / 2) * (L.n + 1) * (L.n + 1);
-    return (unsigned)((slots + CTPB - 1) / CTPB);
-}
 
 static std::atomic<long long> g_launches{0};
 void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
@@ -573,30 +583,30 @@ template <typename T, int FORM>
 static void velocity_pass(const Hier& H, int l, int colour, T* x, const T* f, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
-    const unsigned grid = colour_blocks(L);
+    const long long slots = colour_slots(L.n + 1);
     const int cnt = L.n_spec_vel[colour];
+    const int* list = L.spec_vel[colour];
     T* tmp = spec_scratch<T>(L);
-    count_launches((FORM == FORM_SYM ? 2 : 1) + (cnt ? 2 : 0));
-    if (cnt) k_spec_rows<T, 1><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, cf_vel<T>(L, colour), x, tmp, f);
+    count_launches((FORM == FORM_SYM ? 2 : 1) + (cnt ? 1 : 0));
+    if (cnt) k_spec_rows<T, 1><<<blocks_for(4LL * cnt), TPB, 0, s>>>(V, list, cnt, cf_vel<T>(L, colour), x, tmp, f);
     if (FORM == FORM_SYM) {
         T* out = sym_scratch<T>(L);
-        k_vel_uniform<T, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, out);
-        k_vel_copy_colour<T><<<grid, CTPB, 0, s>>>(V, colour, out, x);
+        k_vel_uniform<T, FORM><<<blocks_for(slots, CTPB), CTPB, 0, s>>>(V, colour, x, f, out, list, 0, tmp);
+        k_vel_copy_colour<T><<<blocks_for(slots + cnt, CTPB), CTPB, 0, s>>>(V, colour, out, x, list, cnt, tmp);
     } else {
-        k_vel_uniform<T, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, nullptr);
+        k_vel_uniform<T, FORM><<<blocks_for(slots + cnt, CTPB), CTPB, 0, s>>>(V, colour, x, f, nullptr, list, cnt, tmp);
     }
-    if (cnt) k_vel_scatter<T><<<blocks_for(cnt), TPB, 0, s>>>(L.spec_vel[colour], cnt, tmp, x, L.nn);
 }
 
 template <typename T>
 static void pressure_pass(const Hier& H, int l, int colour, T* x, const T* g, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
-    const unsigned grid = colour_blocks(L);
+    const long long slots = colour_slots(L.n + 1);
     const int cnt = L.n_spec_pre[colour];
-    count_launches(1 + (cnt ? 1 : 0));
-    if (cnt) k_spec_rows<T, 2><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_pre[colour], cnt, cf_pre<T>(L, colour), x, nullptr, g);
-    k_pre_uniform<T><<<grid, CTPB, 0, s>>>(V, colour, x, g);
+    count_launches(1);
+    k_pre_uniform<T><<<blocks_for(4LL * cnt + slots, CTPB), CTPB, 0, s>>>(V, colour, x, g, L.spec_pre[colour], cnt,
+                                                                          cf_pre<T>(L, colour));
 }
 
 template <typename T>
@@ -879,12 +889,11 @@ static void velocity_pass_static(const Hier& H, int l, int colour, double* x, co
                                  double* tmp, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<double> V = view<double>(H, l);
-    const unsigned grid = colour_blocks(L);
     const int cnt = L.n_spec_vel[colour];
-    count_launches(1 + (cnt ? 2 : 0));
+    count_launches(1 + (cnt ? 1 : 0));
     if (cnt) k_spec_rows<double, 1><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, L.cf_vel_d[colour], x, tmp, f);
-    k_vel_uniform<double, FORM><<<grid, CTPB, 0, s>>>(V, colour, x, f, nullptr);
-    if (cnt) k_vel_scatter<double><<<blocks_for(cnt), TPB, 0, s>>>(L.spec_vel[colour], cnt, tmp, x, L.nn);
+    k_vel_uniform<double, FORM><<<blocks_for(colour_slots(L.n + 1) + cnt, CTPB), CTPB, 0, s>>>(
+        V, colour, x, f, nullptr, L.spec_vel[colour], cnt, tmp);
 }
 
 int launch_velocity_pass_noalloc(const Hier& H, int l, int colour, double* x, const double* b,
