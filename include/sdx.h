@@ -212,8 +212,8 @@ typedef struct sdx_batch* sdx_batch_t; /* opaque, library-owned */
 
 /* Build the hierarchies of descs[0..count-1] (1 <= count <= 256) and the batch's own
  * concatenated work vectors.  autotune != 0 times candidate block shapes (64..512 threads per
- * block, persistent or one-block-per-tile grids) of the colour-pass and residual launches
- * on every level and keeps the fastest.  Synchronous.  Errors as sdx_create, plus SDX_EINVAL
+ * block, persistent grids of one or two waves of resident blocks) of the colour-pass and
+ * residual launches on every level and keeps the fastest.  Synchronous.  Errors as sdx_create, plus SDX_EINVAL
  * when the descriptors disagree on form, coarse_form or prec.  On error *out is NULL. */
 int sdx_batch_create(const sdx_desc* descs, int count, int autotune, sdx_batch_t* out);
 

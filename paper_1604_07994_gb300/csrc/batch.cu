@@ -54,6 +54,8 @@ enum WorkKind {
     WK_CZERO,      // coarsest level: 4 x nodes
     WK_V4,         // finest level: 4 x nodes (vector operations of the outer iteration)
     WK_DOT,        // finest level: 4 x nodes in tiles of DOT_TPB * DOT_IPT (reductions)
+    WK_VPASS0, WK_VPASS1,  // colour slots + staged special rows of the colour (velocity pass)
+    WK_PPASS0, WK_PPASS1,  // 4 x special pressure rows + colour slots (pressure pass)
     WK_COUNT
 };
 
@@ -110,25 +112,55 @@ __global__ void kb_vel_uniform(const BDesc<T>* __restrict__ D, BatchArgs a, int 
     BATCH_END
 }
 
-template <typename T>
-__global__ void kb_vel_copy(const BDesc<T>* __restrict__ D, BatchArgs a, int colour,
-                            const T* __restrict__ src, T* __restrict__ x) {
+// Velocity pass of a colour, uniform rows and the scatter of the colour's staged special rows in
+// one launch (items: colour slots, then special rows); valid for a_tr and the gradient form,
+// whose uniform rows read no velocity of their own colour.
+template <typename T, int FORM>
+__global__ void kb_vel_pass(const BDesc<T>* __restrict__ D, BatchArgs a, int colour, int sl,
+                            T* __restrict__ x, const T* __restrict__ f, const T* __restrict__ tmp) {
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
+    const long long slots = colour_slots(V.n1);
     int i, j, k;
-    if (item >= colour_slots(V.n1) || !colour_slot(V.n1, colour, item, i, j, k)) continue;
-    vel_copy_node<T>(V, i, j, k, src + 3 * d.offn, x + 4 * d.offn);
+    if (item < slots) {
+        if (colour_slot(V.n1, colour, item, i, j, k))
+            vel_uniform_node<T, FORM>(V, i, j, k, x + 4 * d.offn, f + 4 * d.offn, nullptr);
+    } else if (item < slots + d.cnt[sl]) {
+        vel_scatter_slot<T>(d.list[sl], (int)(item - slots), tmp + 3 * d.off_tmp, x + 4 * d.offn, V.nn);
+    }
     BATCH_END
 }
 
+// Strain form: copy the colour's new uniform values back and scatter its special rows.
 template <typename T>
-__global__ void kb_pre_uniform(const BDesc<T>* __restrict__ D, BatchArgs a, int colour,
-                               T* __restrict__ x, const T* __restrict__ b) {
+__global__ void kb_vel_finish(const BDesc<T>* __restrict__ D, BatchArgs a, int colour, int sl,
+                              const T* __restrict__ src, T* __restrict__ x, const T* __restrict__ tmp) {
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
+    const long long slots = colour_slots(V.n1);
     int i, j, k;
-    if (item >= colour_slots(V.n1) || !colour_slot(V.n1, colour, item, i, j, k)) continue;
-    pre_uniform_node<T>(V, i, j, k, x + 4 * d.offn, b + 4 * d.offn + 3 * V.nn);
+    if (item < slots) {
+        if (colour_slot(V.n1, colour, item, i, j, k)) vel_copy_node<T>(V, i, j, k, src + 3 * d.offn, x + 4 * d.offn);
+    } else if (item < slots + d.cnt[sl]) {
+        vel_scatter_slot<T>(d.list[sl], (int)(item - slots), tmp + 3 * d.off_tmp, x + 4 * d.offn, V.nn);
+    }
+    BATCH_END
+}
+
+// Pressure pass of a colour in one launch: special rows (a quad of lanes each, first) and the
+// uniform nodes, both in place (they read p only at the other colour).
+template <typename T>
+__global__ void kb_pre_pass(const BDesc<T>* __restrict__ D, BatchArgs a, int colour, int sl,
+                            T* __restrict__ x, const T* __restrict__ b) {
+    BATCH_TILES(D, a)
+    const LevelView<T> V = d.V;
+    const int cnt = d.cnt[sl];
+    T* xv = x + 4 * d.offn;
+    const T* g = b + 4 * d.offn + 3 * V.nn;
+    int i, j, k;
+    if (item < 4LL * cnt) spec_row_quad<T, 2>(V, d.list[sl], cnt, d.cf[sl], xv, nullptr, g, item);
+    else if (item - 4LL * cnt < colour_slots(V.n1) && colour_slot(V.n1, colour, item - 4LL * cnt, i, j, k))
+        pre_uniform_node<T>(V, i, j, k, xv, g);
     BATCH_END
 }
 
@@ -161,15 +193,6 @@ __global__ void kb_spec(const BDesc<T>* __restrict__ D, BatchArgs a, int sl, T* 
     else
         spec_row_quad<T, MODE>(V, d.list[sl], cnt, d.cf[sl], xv, y + 4 * d.offn, b ? b + 4 * d.offn : nullptr,
                                item);
-    BATCH_END
-}
-
-template <typename T>
-__global__ void kb_vel_scatter(const BDesc<T>* __restrict__ D, BatchArgs a, int sl,
-                               const T* __restrict__ tmp, T* __restrict__ x) {
-    BATCH_TILES(D, a)
-    if (item >= d.cnt[sl]) continue;
-    vel_scatter_slot<T>(d.list[sl], (int)item, tmp + 3 * d.off_tmp, x + 4 * d.offn, d.V.nn);
     BATCH_END
 }
 
@@ -548,27 +571,25 @@ template <typename T, int FORM>
 static void bvel_pass(Batch& B, int l, int colour, T* x, const T* f, cudaStream_t s) {
     BLevel& L = B.lv[l];
     const Work& ws = L.w[WK_VEL0 + colour];
-    const Work& wu = L.w[WK_SLOTS];
+    const Work& wp = L.w[WK_VPASS0 + colour];
     BDesc<T>* D = dtab<T>(L);
     const int sl = colour ? SL_VEL1 : SL_VEL0;
     blaunch(ws, s, kb_spec<T, 1>, D, args(B, ws, B.active), sl, x, vtmp<T>(L), f);
     if (FORM == FORM_SYM) {
+        const Work& wu = L.w[WK_SLOTS];
         blaunch(wu, s, kb_vel_uniform<T, FORM>, D, args(B, wu, B.active), colour, x, f, vsym<T>(L));
-        blaunch(wu, s, kb_vel_copy<T>, D, args(B, wu, B.active), colour, (const T*)vsym<T>(L), x);
+        blaunch(wp, s, kb_vel_finish<T>, D, args(B, wp, B.active), colour, sl, (const T*)vsym<T>(L), x,
+                (const T*)vtmp<T>(L));
     } else {
-        blaunch(wu, s, kb_vel_uniform<T, FORM>, D, args(B, wu, B.active), colour, x, f, (T*)nullptr);
+        blaunch(wp, s, kb_vel_pass<T, FORM>, D, args(B, wp, B.active), colour, sl, x, f, (const T*)vtmp<T>(L));
     }
-    blaunch(ws, s, kb_vel_scatter<T>, D, args(B, ws, B.active), sl, (const T*)vtmp<T>(L), x);
 }
 
 template <typename T>
 static void bpre_pass(Batch& B, int l, int colour, T* x, const T* b, cudaStream_t s) {
     BLevel& L = B.lv[l];
-    const Work& ws = L.w[WK_PRE0 + colour];
-    const Work& wu = L.w[WK_SLOTS];
-    BDesc<T>* D = dtab<T>(L);
-    blaunch(ws, s, kb_spec<T, 2>, D, args(B, ws, B.active), colour ? SL_PRE1 : SL_PRE0, x, (T*)nullptr, b);
-    blaunch(wu, s, kb_pre_uniform<T>, D, args(B, wu, B.active), colour, x, b);
+    const Work& wp = L.w[WK_PPASS0 + colour];
+    blaunch(wp, s, kb_pre_pass<T>, dtab<T>(L), args(B, wp, B.active), colour, colour ? SL_PRE1 : SL_PRE0, x, b);
 }
 
 template <typename T>
@@ -787,6 +808,10 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
                     L.w[WK_VEL1].items[i] = 4LL * Li.n_spec_vel[1];
                     L.w[WK_PRE0].items[i] = 4LL * Li.n_spec_pre[0];
                     L.w[WK_PRE1].items[i] = 4LL * Li.n_spec_pre[1];
+                    for (int c = 0; c < 2; ++c) {
+                        L.w[WK_VPASS0 + c].items[i] = colour_slots(Li.n + 1) + Li.n_spec_vel[c];
+                        L.w[WK_PPASS0 + c].items[i] = colour_slots(Li.n + 1) + 4LL * Li.n_spec_pre[c];
+                    }
                 }
                 // the finest level also serves the outer iteration (residuals of every instance)
                 if (l == 0) {
@@ -851,7 +876,8 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
         // default shapes: 128-thread colour passes, 256 elsewhere, grids capped at the resident capacity
         for (BLevel& L : B->lv)
             for (int k = 0; k < WK_COUNT; ++k) {
-                const int tpb = k == WK_SLOTS ? 128 : (k == WK_DOT ? DOT_TPB : 256);
+                const bool pass = k == WK_SLOTS || k == WK_VPASS0 || k == WK_VPASS1 || k == WK_PPASS0 || k == WK_PPASS1;
+                const int tpb = pass ? 128 : (k == WK_DOT ? DOT_TPB : 256);
                 const long long per = k == WK_DOT ? (long long)DOT_TPB * DOT_IPT : 0;
                 set_work(*B, L.w[k], tpb, 8 * B->sms, per);
             }
@@ -878,23 +904,22 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
 }
 
 // ---------------------------------------------------------------- autotuner
-// For every level, the colour-pass kernels (velocity + pressure, WK_SLOTS) and the residual
-// kernel (WK_NODES) are timed with 64..512 threads per block, each with a persistent grid
-// (resident blocks x SMs) and with one block per tile; the fastest shape is kept.
+// For every level, the colour passes (velocity + pressure; one shape for all pass kinds) and the
+// residual kernel (WK_NODES) are timed with 64..512 threads per block, each with a persistent
+// grid of one or two waves of resident blocks; the fastest shape is kept.
 template <typename T, int FORM>
-static float time_shape(Batch& B, int l, int kind, cudaStream_t s) {
+static float time_shape(Batch& B, int l, bool passes, cudaStream_t s) {
     BLevel& L = B.lv[l];
     BDesc<T>* D = dtab<T>(L);
-    const Work& w = L.w[kind];
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     auto run = [&]() {
-        if (kind == WK_SLOTS) {
-            blaunch(w, s, kb_vel_uniform<T, FORM>, D, args(B, w, B.active), 0, vx<T>(L), (const T*)vb<T>(L),
-                    FORM == FORM_SYM ? vsym<T>(L) : (T*)nullptr);
-            blaunch(w, s, kb_pre_uniform<T>, D, args(B, w, B.active), 0, vx<T>(L), (const T*)vb<T>(L));
+        if (passes) {
+            bvel_pass<T, FORM>(B, l, 0, vx<T>(L), (const T*)vb<T>(L), s);
+            bpre_pass<T>(B, l, 0, vx<T>(L), (const T*)vb<T>(L), s);
         } else {
+            const Work& w = L.w[WK_NODES];
             blaunch(w, s, kb_apply_uniform<T, FORM>, D, args(B, w, B.active), (const T*)vx<T>(L), vr<T>(L),
                     (const T*)vb<T>(L));
         }
@@ -918,29 +943,41 @@ static void tune_level(Batch& B, int l) {
     CK(cudaMemset(vx<T>(L), 0, sizeof(T) * v4));
     CK(cudaMemset(vb<T>(L), 0, sizeof(T) * v4));
     const int tpbs[4] = {64, 128, 256, 512};
-    for (int kind : {WK_SLOTS, WK_NODES}) {
-        Work& w = L.w[kind];
-        if (!w.total) continue;
+    const int pass_kinds[5] = {WK_SLOTS, WK_VPASS0, WK_VPASS1, WK_PPASS0, WK_PPASS1};
+    for (bool passes : {true, false}) {
+        if (!(passes ? L.w[WK_VPASS0].total : L.w[WK_NODES].total)) continue;
         float best = 1e30f;
-        int best_tpb = w.tpb, best_cap = 8 * B.sms;
+        int best_tpb = 128, best_cap = 8 * B.sms;
         for (int tpb : tpbs) {
             // every kernel of the kind must be able to launch with this block size
-            int res = kind == WK_SLOTS
-                          ? std::min(max_active_blocks((const void*)kb_vel_uniform<T, FORM>, tpb),
-                                     max_active_blocks((const void*)kb_pre_uniform<T>, tpb))
-                          : std::min(max_active_blocks((const void*)kb_apply_uniform<T, FORM>, tpb),
-                                     max_active_blocks((const void*)kb_prolong<T>, tpb));
-            if (kind == WK_SLOTS && FORM == FORM_SYM)
-                res = std::min(res, max_active_blocks((const void*)kb_vel_copy<T>, tpb));
+            int res;
+            if (passes) {
+                res = std::min(max_active_blocks((const void*)kb_vel_pass<T, FORM>, tpb),
+                               max_active_blocks((const void*)kb_pre_pass<T>, tpb));
+                if (FORM == FORM_SYM)
+                    res = std::min(res, std::min(max_active_blocks((const void*)kb_vel_uniform<T, FORM>, tpb),
+                                                 max_active_blocks((const void*)kb_vel_finish<T>, tpb)));
+            } else {
+                res = std::min(max_active_blocks((const void*)kb_apply_uniform<T, FORM>, tpb),
+                               max_active_blocks((const void*)kb_prolong<T>, tpb));
+            }
             if (res < 1) continue;
-            for (int cap : {res * B.sms, 1 << 30}) {
-                set_work(B, w, tpb, cap);
-                const float ms = time_shape<T, FORM>(B, l, kind, 0);
+            // persistent grids only: when most instances have converged, a grid of one block per
+            // tile would launch every masked tile's block just to skip it
+            for (int cap : {res * B.sms, 2 * res * B.sms}) {
+                if (passes)
+                    for (int k : pass_kinds) set_work(B, L.w[k], tpb, cap);
+                else
+                    set_work(B, L.w[WK_NODES], tpb, cap);
+                const float ms = time_shape<T, FORM>(B, l, passes, 0);
                 if (cudaGetLastError() != cudaSuccess) continue;  // shape rejected at launch
                 if (ms < best) { best = ms; best_tpb = tpb; best_cap = cap; }
             }
         }
-        set_work(B, w, best_tpb, best_cap);
+        if (passes)
+            for (int k : pass_kinds) set_work(B, L.w[k], best_tpb, best_cap);
+        else
+            set_work(B, L.w[WK_NODES], best_tpb, best_cap);
     }
 }
 
@@ -1188,8 +1225,8 @@ int sdx_batch_shape(sdx_batch_t b, int level, int* tpb_pass, int* grid_pass, int
     Batch* B = as_batch(b);
     if (!B || level < 0 || level >= (int)B->lv.size()) { set_error("bad batch or level"); return SDX_EINVAL; }
     const BLevel& L = B->lv[level];
-    if (tpb_pass) *tpb_pass = L.w[WK_SLOTS].tpb;
-    if (grid_pass) *grid_pass = L.w[WK_SLOTS].grid;
+    if (tpb_pass) *tpb_pass = L.w[WK_VPASS0].tpb;
+    if (grid_pass) *grid_pass = L.w[WK_VPASS0].grid;
     if (tpb_residual) *tpb_residual = L.w[WK_NODES].tpb;
     if (grid_residual) *grid_residual = L.w[WK_NODES].grid;
     return SDX_OK;
