@@ -406,6 +406,8 @@ struct CoopArgs {
     T* tmp;       // staged special velocity values (3 per row)
     T* sym;       // strain form: new values of the uniform nodes (3 components)
     unsigned* bar;  // [2]: arrivals, generation
+    unsigned extra; // arrivals a barrier waits for beyond the grid's blocks (0; > 0 only to test
+                    // that a barrier which cannot complete times out and reports it)
     int* err;
 };
 
@@ -427,7 +429,7 @@ __device__ __forceinline__ void uzawa_coop_body(const CoopArgs<T>& a) {
     const long long nth = (long long)gridDim.x * blockDim.x;
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long slots = colour_slots(L.n1);
-    const unsigned nb = gridDim.x;
+    const unsigned nb = gridDim.x + a.extra;
     T* x = a.x;
     const T* b = a.b;
     const T* g = b + 3 * L.nn;
@@ -640,6 +642,7 @@ static CoopArgs<T> coop_args(const Hier& H, int l, T* x, const T* b, int steps) 
     a.sym = sym_scratch<T>(L);
     a.bar = H.coop_bar;
     a.err = H.coop_err;
+    a.extra = H.coop_barrier_extra;
     return a;
 }
 

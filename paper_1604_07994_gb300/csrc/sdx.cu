@@ -397,6 +397,7 @@ Hier* hier_create(const sdx_desc* d) {
         H->use_coop = !(nc && nc[0] == '1');
         if (const char* cm = std::getenv("SDX_COOP_MAX_NODES")) H->coop_max_nodes = std::atoll(cm);
         if (const char* cm = std::getenv("SDX_CLUSTER_MAX_NODES")) H->cluster_max_nodes = std::atoll(cm);
+        if (const char* cm = std::getenv("SDX_TEST_BARRIER_EXTRA")) H->coop_barrier_extra = (unsigned)std::atoi(cm);
         H->coop_bar = dalloc<unsigned>(2);
         H->coop_err = dalloc<int>(1);
         CK(cudaMemset(H->coop_bar, 0, 2 * sizeof(unsigned)));

@@ -127,6 +127,7 @@ struct Hier {
     long long cluster_max_nodes = CLUSTER_MAX_NODES;
     unsigned* coop_bar = nullptr;   // grid barrier state of the cooperative smoother [2]
     int* coop_err = nullptr;        // set when a barrier wait of that smoother timed out
+    unsigned coop_barrier_extra = 0;  // test hook: barrier arrivals that never come (> 0 forces time-outs)
 };
 
 template <typename T>

@@ -269,3 +269,27 @@ def test_fused_smoothing_launches_match_per_pass_kernels(sdx, name, prec, monkey
         out[tag] = _host(x)
         H.close()
     assert np.array_equal(out["per_pass"], out["fused"])
+
+
+def test_stuck_grid_barrier_times_out_and_reports(sdx, monkeypatch):
+    """A grid barrier of the cooperative smoother that cannot complete (it waits for one more
+    block than the grid has: a flag that nothing sets) gives up after its bounded wait, the
+    solve returns SDX_ETIMEOUT, and the device stays usable for the next hierarchy."""
+    p = PROBLEMS["cube16"]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    b = _dev(d.rhs(p.nodal_forcing()))
+    for k in ("SDX_NO_COOP", "SDX_CLUSTER_MAX_NODES"):
+        monkeypatch.delenv(k, raising=False)
+    monkeypatch.setenv("SDX_COOP_MAX_NODES", "200000")
+    monkeypatch.setenv("SDX_TEST_BARRIER_EXTRA", "1")
+    H = sdx.Hierarchy.from_problem(p, form="tr", prec=0)
+    x = _dev(np.zeros(4 * p.nodes))
+    with pytest.raises(sdx.SdxError) as e:
+        H.sdx_solve(b, x, rtol=1e-8, maxit=5, outer=sdx.OUTER_VCYCLE)
+    assert e.value.code == sdx.ETIMEOUT
+    H.close()
+    monkeypatch.delenv("SDX_TEST_BARRIER_EXTRA")
+    H = sdx.Hierarchy.from_problem(p, form="tr", prec=0)
+    x = _dev(np.zeros(4 * p.nodes))
+    st = H.sdx_solve(b, x, rtol=1e-8, maxit=100, outer=sdx.OUTER_FGMRES)
+    assert st["res"] <= 1e-8 * st["bnorm"]
