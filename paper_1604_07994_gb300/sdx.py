@@ -346,9 +346,11 @@ class Batch:
         _check(load().sdx_batch_vcycle(self._h, _ptr_array(b_list), _ptr_array(x_list), _stream(stream)))
 
     def sdx_batch_solve(self, b_list, x_list, rtol=1e-8, maxit=200, restart=30, stream=None,
-                        allow_noconv=False):
+                        allow_noconv=False, allow_codes=()):
+        """Per-instance stats; a return code outside (OK, ENOCONV if allow_noconv, allow_codes)
+        raises SdxError (each instance's own code is in its stats' "status")."""
         st = (sdx_stats * self.count)()
-        allow = (OK, ENOCONV) if allow_noconv else (OK,)
+        allow = ((OK, ENOCONV) if allow_noconv else (OK,)) + tuple(allow_codes)
         _check(load().sdx_batch_solve(self._h, _ptr_array(b_list), _ptr_array(x_list), float(rtol),
                                       int(maxit), int(restart), st, _stream(stream)), allow)
         return [st[i].as_dict() for i in range(self.count)]

@@ -171,3 +171,18 @@ def test_batch_benchmark_sizes_reach_tolerance(sdx):
         rel = float(torch.linalg.norm(r) / torch.linalg.norm(b))
         assert st["status"] == 0 and rel <= SOLVE_TOL, (p.name, rel, st)
         H.close()
+
+
+def test_batch_statuses_are_per_instance(sdx):
+    """A NaN in one instance's right-hand side marks that instance SDX_ENONFINITE (and the call
+    returns it) while the other instance still converges in the same batch."""
+    probs = [W.cube_inclusion(8, 4), W.random_instance(12, 3, 9, 3, log10_contrast=(0, 4))]
+    B = sdx.Batch(probs, prec=1, autotune=False)
+    b0, d0 = _rhs(probs[0])
+    b1, _ = _rhs(probs[1])
+    b0[np.flatnonzero(~d0.constrained())[5]] = np.inf
+    bs = [_dev(b0), _dev(b1)]
+    xs = [_dev(np.zeros_like(b0)), _dev(np.zeros_like(b1))]
+    st = B.sdx_batch_solve(bs, xs, rtol=1e-10, maxit=100, allow_codes=(sdx.ENONFINITE,))
+    assert st[0]["status"] == sdx.ENONFINITE
+    assert st[1]["status"] == 0 and st[1]["res"] <= 1e-10 * st[1]["bnorm"]

@@ -293,3 +293,25 @@ def test_stuck_grid_barrier_times_out_and_reports(sdx, monkeypatch):
     x = _dev(np.zeros(4 * p.nodes))
     st = H.sdx_solve(b, x, rtol=1e-8, maxit=100, outer=sdx.OUTER_FGMRES)
     assert st["res"] <= 1e-8 * st["bnorm"]
+
+
+def test_nonfinite_rhs_and_iteration_cap_are_reported(sdx):
+    """A NaN planted in the right-hand side on the host is caught by the norm kernel
+    (SDX_ENONFINITE); a solve stopped by maxit returns SDX_ENOCONV with its statistics filled
+    and the last iterate in x (its residual below the initial one)."""
+    p = PROBLEMS["cube16"]
+    d = Discretisation(p.n, p.cell_mu().ravel(), p.face)
+    b = d.rhs(p.nodal_forcing())
+    H = sdx.Hierarchy.from_problem(p)
+    bad = b.copy()
+    bad[np.flatnonzero(~d.constrained())[10]] = np.nan
+    x = _dev(np.zeros_like(b))
+    with pytest.raises(sdx.SdxError) as e:
+        H.sdx_solve(_dev(bad), x, rtol=1e-8, maxit=10, outer=sdx.OUTER_FGMRES)
+    assert e.value.code == sdx.ENONFINITE
+    x = _dev(np.zeros_like(b))
+    st = H.sdx_solve(_dev(b), x, rtol=1e-14, maxit=2, outer=sdx.OUTER_VCYCLE, allow_noconv=True)
+    assert st["status"] == sdx.ENOCONV and st["iterations"] == 2 and st["res"] < 0.5 * st["res0"]
+    r = torch.empty_like(x)
+    H.sdx_residual(0, _dev(b), x, r)
+    assert abs(float(torch.linalg.norm(r)) - st["res"]) <= 1e-12 * st["res0"]
