@@ -189,7 +189,13 @@ int sdx_vcycle(sdx_hier_t h, const double* b, double* x, void* stream);
  * outer: SDX_OUTER_VCYCLE or SDX_OUTER_FGMRES (restart = Krylov basis size, >= 1; ignored
  * for V-cycles).  Synchronises the stream once per iteration to test convergence.  stats may
  * be NULL.  Returns SDX_ENOCONV if maxit iterations did not meet rtol, SDX_ENONFINITE if a
- * residual norm was NaN/Inf (x is then the last finite iterate or garbage, stats filled). */
+ * residual norm was NaN/Inf (x is then the last finite iterate or garbage, stats filled),
+ * SDX_ETIMEOUT if a fused smoothing launch gave up a grid barrier after its bounded wait
+ * (reported at the next synchronisation; x is then not meaningful).
+ * The smoothing steps of small levels may run fused in one launch (one thread-block cluster
+ * for FP32 levels of at most 10000 nodes; a cooperative grid launch when the environment
+ * variable SDX_COOP_MAX_NODES is set to a node limit when the hierarchy is created; none when
+ * SDX_NO_COOP=1); every variant gives the same bits as the per-pass launches. */
 int sdx_solve(sdx_hier_t h, const double* b, double* x, double rtol, int maxit, int outer,
               int restart, sdx_stats* stats, void* stream);
 
