@@ -315,3 +315,37 @@ def test_nonfinite_rhs_and_iteration_cap_are_reported(sdx):
     r = torch.empty_like(x)
     H.sdx_residual(0, _dev(b), x, r)
     assert abs(float(torch.linalg.norm(r)) - st["res"]) <= 1e-12 * st["res0"]
+
+
+def test_full_size_top_layer_256(sdx):
+    """256^3 cells, top layer of viscosity 1e3, traction-free top, free-slip sides, no-slip
+    bottom (the mixed-precision workload): sampled rows of the FP64 apply against the oracle's
+    row evaluation (interior, layer interface, traction and free-slip faces), and the
+    FP32-refined solve, whose final residual recomputed in FP64 meets 1e-8."""
+    p = W.top_layer(256, 8)
+    cm = p.cell_mu().ravel()
+    nn = p.nodes
+    n1 = p.n + 1
+    H = sdx.Hierarchy.from_problem(p, form="tr", coarse_form="sym", prec=1)
+    con = H.sdx_constraint_mask(0)
+    x = W.random_vector(p.n, 31).ravel()
+    x[con] = 0.0
+    y = _dev(np.zeros_like(x))
+    H.sdx_apply(0, _dev(x), y)
+    yh = _host(y).reshape(4, nn)
+    rng = np.random.Generator(np.random.PCG64(32))
+    i, j = rng.integers(0, n1, 100), rng.integers(0, n1, 100)
+    top = i + n1 * (j + n1 * p.n)                       # traction face
+    iface = i + n1 * (j + n1 * (7 * p.n // 8))          # viscosity interface plane
+    side = 0 + n1 * (j + n1 * rng.integers(0, n1, 100))  # free-slip face x = 0
+    nodes = np.concatenate([rng.integers(0, nn, 200), top, iface, side])
+    ys = sampled_rows(p.n, cm, p.face, "tr", x, nodes)
+    assert np.abs(ys - yh[:, nodes]).max() <= APPLY_TOL * np.abs(yh).max()
+    f = _dev(p.nodal_forcing().ravel())
+    b = torch.zeros(4 * nn, dtype=torch.float64, device="cuda")
+    H.sdx_rhs(f, b)
+    xs = torch.zeros_like(b)
+    st = H.sdx_solve(b, xs, rtol=1e-8, maxit=200, outer=sdx.OUTER_FGMRES, restart=30)
+    r = torch.empty_like(b)
+    H.sdx_residual(0, b, xs, r)
+    assert st["status"] == 0 and float(torch.linalg.norm(r)) <= SOLVE_TOL * float(torch.linalg.norm(b))
