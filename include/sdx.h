@@ -68,7 +68,8 @@ extern "C" {
 typedef struct sdx_hier* sdx_hier_t; /* opaque, library-owned hierarchy */
 
 typedef struct {
-    int n;                  /* cells per side on the finest grid; n = n_coarse * 2^k, k >= 0 */
+    int n;                  /* cells per side on the finest grid; n = n_coarse * 2^k, k >= 0,
+                               n <= 1024 */
     int n_coarse;           /* cells per side on the coarsest grid (>= 2); every viscosity
                                interface must lie on a plane of that grid */
     const uint8_t* cell_id; /* HOST array of n^3 subdomain ids, cell (i,j,k) at

@@ -315,7 +315,8 @@ void hier_free(Hier* H) {
 
 Hier* hier_create(const sdx_desc* d) {
     if (!d || !d->cell_id || !d->mu) { set_error("null descriptor or array"); throw Fail{SDX_EINVAL}; }
-    if (d->n < 2 || d->n_coarse < 2 || d->n > 2048) { set_error("n and n_coarse must be >= 2 (n <= 2048)"); throw Fail{SDX_EINVAL}; }
+    // node indices of the special-row lists are 32-bit: (n + 1)^3 < 2^31 holds up to n = 1024
+    if (d->n < 2 || d->n_coarse < 2 || d->n > 1024) { set_error("n and n_coarse must be >= 2 (n <= 1024)"); throw Fail{SDX_EINVAL}; }
     {
         int m = d->n;
         while (m > d->n_coarse && m % 2 == 0) m /= 2;

@@ -61,6 +61,10 @@ def test_strerror_and_argument_validation_without_a_device():
     d.form, d.coarse_form, d.prec, d.pspg_beta = 0, -1, 0, 1.0 / 12
     assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
     assert b"n_coarse" in lib.sdx_last_error()
+    d.n, d.n_coarse = 2048, 8  # beyond the 32-bit node indices of the special-row lists
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert b"1024" in lib.sdx_last_error()
+    d.n, d.n_coarse = 6, 4
     d.n, d.n_coarse, d.n_mu = 8, 4, 2
     cells8 = np.zeros(8 ** 3, dtype=np.uint8)
     d.cell_id = cells8.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
