@@ -134,6 +134,33 @@ class Discretisation:
         np.add.at(m, self.tets.ravel(), np.repeat(self.vol / 4.0, 4))
         return m
 
+    def mass_matrix(self, weight_T: np.ndarray = None) -> sp.csr_matrix:
+        """Consistent P1 mass matrix [nn, nn]: M[b, a] = sum_T w_T int_T lambda_a lambda_b
+        = sum_T w_T |T| (1 + delta_ab) / 20, with w_T = 1 unless a per-tetrahedron weight is
+        given."""
+        w = self.vol if weight_T is None else self.vol * np.asarray(weight_T, dtype=np.float64)
+        nT = self.tets.shape[0]
+        loc = (np.ones((4, 4)) + np.eye(4)) / 20.0
+        ent = w[:, None, None] * loc[None, :, :]
+        rows = np.broadcast_to(self.tets[:, :, None], (nT, 4, 4))
+        cols = np.broadcast_to(self.tets[:, None, :], (nT, 4, 4))
+        return self._assemble(ent, rows, cols, (self.nn, self.nn))
+
+    def paper_norms(self, x: np.ndarray) -> np.ndarray:
+        """The three norms of a discrete pair (u, p) (SoA [4nn]) used in the error tables of
+        Sec. 4.2: ||u||_0 (L2 of the P1 velocity field), ||u||_V with ||v||_V^2 = a_sym(v, v)
+        and ||p||_Q with ||q||_Q^2 = (q / (2 mu), q)_0, the norms defined in Sec. 3 before
+        Lemma 3.  Returns [||u||_0, ||u||_V, ||p||_Q]."""
+        nn = self.nn
+        x = np.asarray(x, dtype=np.float64).ravel()
+        u = x[: 3 * nn]
+        p = x[3 * nn:]
+        M = self.mass_matrix()
+        l2 = np.sqrt(sum(u[c * nn:(c + 1) * nn] @ (M @ u[c * nn:(c + 1) * nn]) for c in range(3)))
+        en = np.sqrt(u @ (self.velocity_block("sym") @ u))
+        q = np.sqrt(p @ (self.mass_matrix(1.0 / (2.0 * self.mu_T)) @ p))
+        return np.array([l2, en, q])
+
     def pressure_weights(self) -> np.ndarray:
         """w_b = int lambda_b / mu = sum_{T ni b} |T| / (4 mu_T): the discrete form of the
         constraint int mu^{-1} q = 0 that fixes the pressure constant (Sec. 1, space Q)."""

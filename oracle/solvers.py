@@ -220,7 +220,8 @@ def fgmres(K, precond, b, free, rtol=1e-8, restart=30, maxit=200, x0=None):
     """Flexible GMRES(restart) with right preconditioning (Saad, SIAM J. Sci. Comput. 14,
     1993), modified Gram-Schmidt, Givens rotations.  Vectors are full-size with zeros at
     constrained DoFs; inner products run over the free DoFs.  Stops when the true residual
-    ||b - K x|| <= rtol ||b||.  Returns (x, list of residual norms, one per iteration)."""
+    ||b - K x|| <= rtol ||b||.  Returns (x, list of true residual norms, one at the start of
+    every restart cycle plus the final one)."""
     x = np.zeros_like(b) if x0 is None else x0.copy()
     bn = np.linalg.norm(b[free])
     hist = []

@@ -236,3 +236,37 @@ def test_prolongation_reproduces_linear_functions():
     lin = lambda X: 1.0 + 2.0 * X[:, 0] - 3.0 * X[:, 1] + 0.5 * X[:, 2]
     assert np.abs(P @ lin(xc) - lin(xf)).max() <= 1e-14
     assert np.all(np.asarray(P.sum(axis=1)).ravel() == 1.0)
+
+
+def test_consistent_mass_integrates_linear_fields_exactly():
+    """A linear field is its own P1 interpolant, so l^T M l is the exact integral of l^2 over
+    the unit cube: a^2 + (b^2+c^2+d^2)/3 + a(b+c+d) + (bc+bd+cd)/2 for l = a+bx+cy+dz.  The row
+    sums of M are the lumped masses; with the weight 1/(2 mu_T) the total is int 1/(2 mu)."""
+    n = 4
+    mu = _random_piecewise_mu(n, 5, lattice=2)
+    d = _disc(n, mu)
+    a, b, c, e = 1.0, 2.0, -3.0, 0.5
+    lin = a + b * d.xyz[:, 0] + c * d.xyz[:, 1] + e * d.xyz[:, 2]
+    exact = a * a + (b * b + c * c + e * e) / 3.0 + a * (b + c + e) + (b * c + b * e + c * e) / 2.0
+    M = d.mass_matrix()
+    assert abs(lin @ (M @ lin) - exact) <= 1e-13 * exact
+    assert np.abs(np.asarray(M.sum(axis=1)).ravel() - d.lumped_mass()).max() <= 1e-16
+    Mq = d.mass_matrix(1.0 / (2.0 * d.mu_T))
+    one = np.ones(d.nn)
+    assert abs(one @ (Mq @ one) - np.sum(1.0 / (2.0 * mu)) / n ** 3) <= 1e-13 * np.sum(1.0 / mu) / n ** 3
+
+
+def test_paper_norms_of_closed_form_fields():
+    """The norms of Sec. 3 on u = x (identity field) and a linear pressure, constant mu:
+    ||u||_0^2 = int |x|^2 = 1, ||u||_V^2 = a_sym(x, x) = 6 mu (sym grad x = I), and
+    ||p||_Q^2 = int p^2 / (2 mu)."""
+    n, mu = 4, 2.5
+    d = _disc(n, np.full(n ** 3, mu))
+    X = _field(d, lambda x, y, z: (x, y, z))
+    p = 1.0 - d.xyz[:, 0]
+    l0, lv, lq = d.paper_norms(np.concatenate([X, p]))
+    assert abs(l0 ** 2 - 1.0) <= 1e-13
+    assert abs(lv ** 2 - 6.0 * mu) <= 1e-12 * 6.0 * mu
+    # int (1 - x)^2 over the unit cube = 1/3
+    assert abs(lq ** 2 - (1.0 / 3.0) / (2.0 * mu)) <= 1e-13
+
