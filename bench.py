@@ -540,6 +540,139 @@ def run_paper(args, sdx, torch, cycles=40):
             res[name] = {"seconds_per_cycle": e0.elapsed_time(e1) / 5e3, "rho": rho}
             H.close()
         out[lvl] = res
+    out["relative_differences"] = run_paper_tables(args, sdx, torch)
+    return out
+
+
+def _kuhn_vertex_offsets():
+    """The six Kuhn tetrahedra of a cube: for each axis permutation s the vertices c, c + e_s1,
+    c + e_s1 + e_s2, c + (1,1,1), as (di, dj, dk) offsets from the cube's lowest corner c."""
+    from itertools import permutations
+    out = []
+    for s in permutations(range(3)):
+        off = [0, 0, 0]
+        verts = [(0, 0, 0)]
+        for ax in s:
+            off[ax] += 1
+            verts.append(tuple(off))
+        out.append(verts)
+    return out
+
+
+def _corner(g, n, d):
+    """View of a nodal grid g [(n+1)^3, index (k, j, i)] at corner d = (di, dj, dk) of every cell."""
+    return g[d[2]:d[2] + n, d[1]:d[1] + n, d[0]:d[0] + n]
+
+
+def _mass_quadratic(torch, v, n, weight):
+    """v^T M_w v for one nodal P1 field v [(n+1)^3] (x fastest): the consistent mass matrix
+    with a per-cell weight w, per tetrahedron |T| w ((sum_a v_a)^2 + sum_a v_a^2) / 20."""
+    g = v.reshape(n + 1, n + 1, n + 1)
+    tot = torch.zeros((), dtype=v.dtype, device=v.device)
+    for verts in _kuhn_vertex_offsets():
+        c = [_corner(g, n, d) for d in verts]
+        s = c[0] + c[1] + c[2] + c[3]
+        q = c[0] * c[0] + c[1] * c[1] + c[2] * c[2] + c[3] * c[3]
+        tot = tot + (weight * (s * s + q)).sum()
+    return tot * (1.0 / (6.0 * n ** 3)) / 20.0
+
+
+def pressure_weights_t(torch, n, cell_mu):
+    """w_b = int lambda_b / mu = sum over the tetrahedra T at node b of |T| / (4 mu_T), the
+    weights of the discrete constraint int p / mu = 0 (cell_mu: [n, n, n] as (k, j, i))."""
+    w = torch.zeros((n + 1,) * 3, dtype=torch.float64, device=cell_mu.device)
+    share = (1.0 / (6.0 * n ** 3) / 4.0) / cell_mu
+    for verts in _kuhn_vertex_offsets():
+        for d in verts:
+            _corner(w, n, d).add_(share)
+    return w.reshape(-1)
+
+
+def table_norms(torch, x, n, cell_mu, apply_sym):
+    """The norms of the paper's error tables (Sec. 3 definitions) of an SoA pair x = (u, p)
+    [4 (n+1)^3]: ||u||_0 (consistent mass), ||u||_V = a_sym(u, u)^(1/2) from apply_sym (the
+    strain-form operator applied to (u, 0)), ||p||_Q = (p / (2 mu), p)_0^(1/2)."""
+    nn = (n + 1) ** 3
+    l2 = sum(float(_mass_quadratic(torch, x[c * nn:(c + 1) * nn], n, 1.0)) for c in range(3)) ** 0.5
+    v = x.clone()
+    v[3 * nn:] = 0.0
+    y = apply_sym(v)
+    en = float(torch.dot(v[:3 * nn], y[:3 * nn])) ** 0.5
+    q = float(_mass_quadratic(torch, x[3 * nn:], n, 0.5 / cell_mu)) ** 0.5
+    return np.array([l2, en, q])
+
+
+def relative_differences(torch, sols, n, cell_mu, apply_sym, ref="strain"):
+    """||X - U|| / ||U|| in the three table norms for every solution X in sols against U =
+    sols[ref], pressures first normalised to int p / mu = 0 (no traction face)."""
+    nn = (n + 1) ** 3
+    w = pressure_weights_t(torch, n, cell_mu)
+    sols = {k: v.clone() for k, v in sols.items()}
+    for v in sols.values():
+        v[3 * nn:] -= torch.dot(w, v[3 * nn:]) / w.sum()
+    U = sols[ref]
+    base = table_norms(torch, U, n, cell_mu, apply_sym)
+    return {k: (table_norms(torch, v - U, n, cell_mu, apply_sym) / base).tolist()
+            for k, v in sols.items() if k != ref}
+
+
+# The paper's P1-P1 relative differences to the strain form on the columns problem (Sec. 4.2.4,
+# tables "columns-laplace-p1p1" and "columns-stencil-p1p1"): [||.||_0, ||.||_V, ||.||_Q].
+PAPER_COLUMNS_P1P1 = {
+    2: {"gradient": [7.4550e-02, 9.2581e-02, 2.7609e-01], "decoupled": [1.3890e-02, 2.4189e-02, 7.7949e-02]},
+    3: {"gradient": [3.0104e-02, 6.0398e-02, 1.8003e-01], "decoupled": [4.2414e-03, 1.2312e-02, 4.8195e-02]},
+    4: {"gradient": [2.1227e-02, 4.7364e-02, 1.1179e-01], "decoupled": [1.1370e-03, 6.2303e-03, 2.5287e-02]},
+    5: {"gradient": [2.0227e-02, 4.3246e-02, 8.0546e-02], "decoupled": [2.9449e-04, 3.1918e-03, 1.3274e-02]},
+    6: {"gradient": [2.0098e-02, 4.2121e-02, 6.9997e-02], "decoupled": [7.5985e-05, 1.6675e-03, 6.8175e-03]},
+}
+
+
+def run_paper_tables(args, sdx, torch, levels=(2, 3, 4, 5, 6)):
+    """The paper's error tables of the columns problem (Sec. 4.2.4) on the GPU path: at level L
+    (4 * 2^L cells per side, coarsest grid 8^3 below level 2's 16^3) solve the strain, decoupled
+    and gradient forms to 1e-10 with FGMRES + V_var(3,3), then report the relative differences
+    of the decoupled and gradient solutions to the strain solution in ||.||_0, ||.||_V and
+    ||.||_Q beside the paper's P1-P1 values."""
+    from paper_1604_07994_gb300 import workloads as W
+    out = {"problem": "viscosity columns (Sec. 4.2.4), FP64, solves to 1e-10",
+           "norms": "[||u||_0, ||u||_V = a_sym(u,u)^1/2, ||p||_Q = (p/(2mu), p)^1/2], relative to the strain solution",
+           "paper_p1p1": {f"L{k}": v for k, v in PAPER_COLUMNS_P1P1.items() if k in levels}}
+    for lvl in levels:
+        n = 4 * 2 ** lvl
+        prob = W.viscosity_columns(n, 8)
+        f = torch.from_numpy(prob.nodal_forcing().ravel()).cuda()
+        cell_mu = torch.from_numpy(np.ascontiguousarray(prob.cell_mu(), dtype=np.float64)).cuda()
+        sols, solves, H_sym = {}, {}, None
+        try:
+            for name, form in (("strain", "sym"), ("decoupled", "tr"), ("gradient", "grad")):
+                H = sdx.Hierarchy.from_problem(prob, form=form, prec=sdx.PREC_FP64)
+                _, nn, _ = H.sdx_level_size(0)
+                b = torch.zeros(4 * nn, dtype=torch.float64, device="cuda")
+                H.sdx_rhs(f, b)
+                x = torch.zeros_like(b)
+                t0 = time.perf_counter()
+                st = H.sdx_solve(b, x, rtol=1e-10, maxit=300, outer=sdx.OUTER_FGMRES, restart=30, allow_noconv=True)
+                torch.cuda.synchronize()
+                solves[name] = {"iterations": st["iterations"], "final_rel_res": st["res"] / st["bnorm"],
+                                "seconds": time.perf_counter() - t0}
+                sols[name] = x
+                if form == "sym":
+                    H_sym = H
+                else:
+                    H.close()
+
+            def apply_sym(v):
+                y = torch.empty_like(v)
+                H_sym.sdx_apply(0, v, y)
+                return y
+
+            out[f"L{lvl}"] = {"cells": n, "solves": solves,
+                              "relative_differences": relative_differences(torch, sols, n, cell_mu, apply_sym)}
+        except Exception as e:  # a measurement block: report, keep the benchmark line
+            out[f"L{lvl}"] = {"cells": n, "solves": solves, "error": repr(e)}
+        finally:
+            if H_sym is not None:
+                H_sym.close()
     return out
 
 
