@@ -541,6 +541,7 @@ def run_paper(args, sdx, torch, cycles=40):
             H.close()
         out[lvl] = res
     out["relative_differences"] = run_paper_tables(args, sdx, torch)
+    out["relative_differences_layers"] = run_paper_tables(args, sdx, torch, problem="layers")
     return out
 
 
@@ -627,19 +628,35 @@ PAPER_COLUMNS_P1P1 = {
 }
 
 
-def run_paper_tables(args, sdx, torch, levels=(2, 3, 4, 5, 6)):
-    """The paper's error tables of the columns problem (Sec. 4.2.4) on the GPU path: at level L
-    (4 * 2^L cells per side, coarsest grid 8^3 below level 2's 16^3) solve the strain, decoupled
-    and gradient forms to 1e-10 with FGMRES + V_var(3,3), then report the relative differences
-    of the decoupled and gradient solutions to the strain solution in ||.||_0, ||.||_V and
-    ||.||_Q beside the paper's P1-P1 values."""
+# The paper's P1-P0 relative differences on the layers problem (Sec. 4.2.3, tables
+# "layers-laplace" and "layers-stencil"; no P1-P1 table is printed for it).
+PAPER_LAYERS_P1P0 = {
+    2: {"gradient": [3.1359e-01, 4.8968e-01, 2.5337e-01], "decoupled": [3.6872e-02, 5.2343e-02, 5.9058e-02]},
+    3: {"gradient": [3.1095e-01, 5.1625e-01, 2.6207e-01], "decoupled": [1.0722e-02, 2.2601e-02, 2.1634e-02]},
+    4: {"gradient": [3.0922e-01, 5.2354e-01, 2.6458e-01], "decoupled": [2.8306e-03, 1.0224e-02, 8.3074e-03]},
+}
+
+
+def run_paper_tables(args, sdx, torch, levels=(2, 3, 4, 5, 6), problem="columns"):
+    """The paper's error tables of the columns problem (Sec. 4.2.4) or the layers problem
+    (Sec. 4.2.3) on the GPU path: at level L (4 * 2^L cells per side, coarsest grid 8^3 below
+    level 2's 16^3) solve the strain, decoupled and gradient forms to 1e-10 with FGMRES +
+    V_var(3,3), then report the relative differences of the decoupled and gradient solutions
+    to the strain solution in ||.||_0, ||.||_V and ||.||_Q beside the paper's values."""
     from paper_1604_07994_gb300 import workloads as W
-    out = {"problem": "viscosity columns (Sec. 4.2.4), FP64, solves to 1e-10",
-           "norms": "[||u||_0, ||u||_V = a_sym(u,u)^1/2, ||p||_Q = (p/(2mu), p)^1/2], relative to the strain solution",
-           "paper_p1p1": {f"L{k}": v for k, v in PAPER_COLUMNS_P1P1.items() if k in levels}}
+    if problem == "columns":
+        make, paper = W.viscosity_columns, {"paper_p1p1": PAPER_COLUMNS_P1P1}
+        title = "viscosity columns (Sec. 4.2.4), FP64, solves to 1e-10"
+    else:
+        make, paper = W.viscosity_layers, {"paper_p1p0": PAPER_LAYERS_P1P0}
+        title = "viscosity layers (Sec. 4.2.3), FP64, solves to 1e-10"
+    out = {"problem": title,
+           "norms": "[||u||_0, ||u||_V = a_sym(u,u)^1/2, ||p||_Q = (p/(2mu), p)^1/2], relative to the strain solution"}
+    for key, tab in paper.items():
+        out[key] = {f"L{k}": v for k, v in tab.items() if k in levels}
     for lvl in levels:
         n = 4 * 2 ** lvl
-        prob = W.viscosity_columns(n, 8)
+        prob = make(n, 8)
         f = torch.from_numpy(prob.nodal_forcing().ravel()).cuda()
         cell_mu = torch.from_numpy(np.ascontiguousarray(prob.cell_mu(), dtype=np.float64)).cuda()
         sols, solves, H_sym = {}, {}, None
