@@ -3,7 +3,9 @@
 Argument marshalling only: every operation runs in the library's CUDA kernels.  Device
 vectors are passed as torch CUDA tensors (float64, contiguous, 4*(n+1)^3 elements, SoA
 u_x, u_y, u_z, p) or raw integer device pointers; the stream defaults to torch's current
-stream.  The library must have been built (``paper_1604_07994_gb300.build.build()``); there
+stream.  A tensor argument must have exactly the entries of its grid level (checked here,
+before the call, since the library receives bare pointers); raw pointers are the caller's
+responsibility.  The library must have been built (``paper_1604_07994_gb300.build.build()``); there
 is no fallback of any kind when it is missing.
 """
 from __future__ import annotations
@@ -143,6 +145,22 @@ def _ptr(t, itemsize: int = 8) -> int:
     return t.data_ptr()
 
 
+def _check_len(t, count: int) -> None:
+    """The C ABI takes bare pointers, so a tensor shorter than its grid would let the kernels
+    run past its end: check the length.  Raw integer pointers are not checked (their extent is
+    the caller's promise)."""
+    if t is not None and not isinstance(t, int) and t.numel() != count:
+        raise ValueError(f"vector has {t.numel()} elements where {count} are needed")
+
+
+def _vecs(*pairs, itemsize: int = 8):
+    """Device pointers of several (tensor, length) arguments; every length is checked before
+    any pointer is taken."""
+    for t, m in pairs:
+        _check_len(t, m)
+    return [_ptr(t, itemsize) for t, _ in pairs]
+
+
 def _stream(stream) -> Optional[int]:
     if stream is None:
         import torch
@@ -229,45 +247,75 @@ class Hierarchy:
         _check(load().sdx_interface_mask(self._h, level, m.ctypes.data))
         return m.astype(bool)
 
+    def _len(self, level: int, comps: int = 4) -> int:
+        """Entries of a vector of `comps` components on grid level `level`."""
+        if level == 0:
+            return comps * self.nn
+        cache = self.__dict__.setdefault("_level_nodes", {})
+        if level not in cache:
+            cache[level] = self.sdx_level_size(level)[1]
+        return comps * cache[level]
+
     # ---------------------------------------------------------------- operations
     def sdx_apply(self, level, x, y, stream=None):
-        _check(load().sdx_apply(self._h, level, _ptr(x), _ptr(y), _stream(stream)))
+        m = self._len(level)
+        px, py = _vecs((x, m), (y, m))
+        _check(load().sdx_apply(self._h, level, px, py, _stream(stream)))
 
     def sdx_residual(self, level, b, x, r, stream=None):
-        _check(load().sdx_residual(self._h, level, _ptr(b), _ptr(x), _ptr(r), _stream(stream)))
+        m = self._len(level)
+        pb, px, pr = _vecs((b, m), (x, m), (r, m))
+        _check(load().sdx_residual(self._h, level, pb, px, pr, _stream(stream)))
 
     def sdx_rhs(self, f, b, stream=None):
-        _check(load().sdx_rhs(self._h, _ptr(f), _ptr(b), _stream(stream)))
+        pf, pb = _vecs((f, self._len(0, 3)), (b, self._len(0)))
+        _check(load().sdx_rhs(self._h, pf, pb, _stream(stream)))
 
     def sdx_uzawa(self, level, b, x, stream=None):
-        _check(load().sdx_uzawa(self._h, level, _ptr(b), _ptr(x), _stream(stream)))
+        m = self._len(level)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_uzawa(self._h, level, pb, px, _stream(stream)))
 
     def sdx_smooth_pass(self, level, which, colour, b, x, stream=None):
-        _check(load().sdx_smooth_pass(self._h, level, which, colour, _ptr(b), _ptr(x), _stream(stream)))
+        m = self._len(level)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_smooth_pass(self._h, level, which, colour, pb, px, _stream(stream)))
 
     def sdx_apply_f32(self, level, x, y, stream=None):
-        _check(load().sdx_apply_f32(self._h, level, _ptr(x, 4), _ptr(y, 4), _stream(stream)))
+        m = self._len(level)
+        px, py = _vecs((x, m), (y, m), itemsize=4)
+        _check(load().sdx_apply_f32(self._h, level, px, py, _stream(stream)))
 
     def sdx_smooth_pass_f32(self, level, which, colour, b, x, stream=None):
-        _check(load().sdx_smooth_pass_f32(self._h, level, which, colour, _ptr(b, 4), _ptr(x, 4), _stream(stream)))
+        m = self._len(level)
+        pb, px = _vecs((b, m), (x, m), itemsize=4)
+        _check(load().sdx_smooth_pass_f32(self._h, level, which, colour, pb, px, _stream(stream)))
 
     def sdx_smooth_pass_noalloc(self, level, colour, b, x, stream=None):
-        _check(load().sdx_smooth_pass_noalloc(self._h, level, colour, _ptr(b), _ptr(x), _stream(stream)))
+        m = self._len(level)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_smooth_pass_noalloc(self._h, level, colour, pb, px, _stream(stream)))
 
     def sdx_restrict(self, level, r_fine, b_coarse, stream=None):
-        _check(load().sdx_restrict(self._h, level, _ptr(r_fine), _ptr(b_coarse), _stream(stream)))
+        pr, pb = _vecs((r_fine, self._len(level)), (b_coarse, self._len(level + 1)))
+        _check(load().sdx_restrict(self._h, level, pr, pb, _stream(stream)))
 
     def sdx_prolong_add(self, level, e_coarse, x_fine, stream=None):
-        _check(load().sdx_prolong_add(self._h, level, _ptr(e_coarse), _ptr(x_fine), _stream(stream)))
+        pe, px = _vecs((e_coarse, self._len(level + 1)), (x_fine, self._len(level)))
+        _check(load().sdx_prolong_add(self._h, level, pe, px, _stream(stream)))
 
     def sdx_vcycle(self, b, x, stream=None):
-        _check(load().sdx_vcycle(self._h, _ptr(b), _ptr(x), _stream(stream)))
+        m = self._len(0)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_vcycle(self._h, pb, px, _stream(stream)))
 
     def sdx_solve(self, b, x, rtol=1e-8, maxit=100, outer=OUTER_FGMRES, restart=30, stream=None,
                   allow_noconv=False) -> dict:
         st = sdx_stats()
         allow = (OK, ENOCONV) if allow_noconv else (OK,)
-        _check(load().sdx_solve(self._h, _ptr(b), _ptr(x), float(rtol), int(maxit), int(outer),
+        m = self._len(0)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_solve(self._h, pb, px, float(rtol), int(maxit), int(outer),
                                 int(restart), ctypes.byref(st), _stream(stream)), allow)
         return st.as_dict()
 
@@ -307,6 +355,7 @@ class Batch:
         _check(lib.sdx_batch_create(descs, len(problems), 1 if autotune else 0, ctypes.byref(h)))
         self._h = h
         self.count = len(problems)
+        self._lens = [4 * self.sdx_batch_size(i)[1] for i in range(self.count)]
 
     def close(self):
         if getattr(self, "_h", None):
@@ -336,6 +385,16 @@ class Batch:
         view.n, view.nn = n, nodes
         return view
 
+    def _ptr_arrays(self, *lists):
+        """Pointer arrays of per-instance vector lists: one vector per instance, each of its
+        instance's length, all checked before any pointer is taken."""
+        for lst in lists:
+            if len(lst) != self.count:
+                raise ValueError(f"{len(lst)} vectors for a batch of {self.count} instances")
+            for t, m in zip(lst, self._lens):
+                _check_len(t, m)
+        return [_ptr_array(lst) for lst in lists]
+
     def sdx_batch_shape(self, level: int):
         v = [ctypes.c_int() for _ in range(4)]
         _check(load().sdx_batch_shape(self._h, level, *[ctypes.byref(x) for x in v]))
@@ -343,7 +402,8 @@ class Batch:
                 "grid_residual": v[3].value}
 
     def sdx_batch_vcycle(self, b_list, x_list, stream=None):
-        _check(load().sdx_batch_vcycle(self._h, _ptr_array(b_list), _ptr_array(x_list), _stream(stream)))
+        pb, px = self._ptr_arrays(b_list, x_list)
+        _check(load().sdx_batch_vcycle(self._h, pb, px, _stream(stream)))
 
     def sdx_batch_solve(self, b_list, x_list, rtol=1e-8, maxit=200, restart=30, stream=None,
                         allow_noconv=False, allow_codes=()):
@@ -351,7 +411,8 @@ class Batch:
         raises SdxError (each instance's own code is in its stats' "status")."""
         st = (sdx_stats * self.count)()
         allow = ((OK, ENOCONV) if allow_noconv else (OK,)) + tuple(allow_codes)
-        _check(load().sdx_batch_solve(self._h, _ptr_array(b_list), _ptr_array(x_list), float(rtol),
+        pb, px = self._ptr_arrays(b_list, x_list)
+        _check(load().sdx_batch_solve(self._h, pb, px, float(rtol),
                                       int(maxit), int(restart), st, _stream(stream)), allow)
         return [st[i].as_dict() for i in range(self.count)]
 
