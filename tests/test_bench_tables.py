@@ -66,3 +66,33 @@ def test_relative_differences_match_the_oracle():
     for k in ("decoupled", "gradient"):
         ref = d.paper_norms(sols[k] - U) / d.paper_norms(U)
         assert np.all(np.abs(np.array(got[k]) / ref - 1.0) <= 1e-10), (k, got[k], ref)
+
+
+def test_vcycle_rate_helper_reproduces_the_oracle_rate():
+    """bench.vcycle_rate (the GPU benchmark's rate measurement, torch) driven by the oracle's
+    V-cycle gives the rate of the oracle's own measurement, and that rate is the paper's
+    (within 10 %: decoupled form 0.241-0.244 in Table timeANDconv)."""
+    from oracle.solvers import Hierarchy
+    from test_oracle_solvers import PAPER_RHO, _asymptotic_rate
+    n = 16
+    p = W.viscosity_columns(n, 4)
+    H = Hierarchy(n, 4, p.cell_mu().ravel(), p.face, "tr")
+    L = H.levels[0]
+    rho_ref, _ = _asymptotic_rate(H)
+    x = W.random_vector(n, 77).ravel()
+    x[L.con] = 0.0
+    xt = torch.from_numpy(x)
+    zero = np.zeros_like(x)
+    cell_mu = torch.from_numpy(np.ascontiguousarray(p.cell_mu(), dtype=np.float64))
+    w = bench.pressure_weights_t(torch, n, cell_mu)
+
+    def vcycle(v):
+        v.copy_(torch.from_numpy(H.vcycle(v.numpy().copy(), zero)))
+
+    def residual(v):
+        return torch.from_numpy(L.residual(v.numpy(), zero))
+
+    rho, rates = bench.vcycle_rate(torch, vcycle, residual, xt, L.nn, w, cycles=25, last=8)
+    assert abs(rho - rho_ref) <= 1e-10 * rho_ref, (rho, rho_ref)
+    lo, hi = PAPER_RHO["tr"]
+    assert 0.9 * lo <= rho <= 1.1 * hi
