@@ -270,3 +270,24 @@ def test_paper_norms_of_closed_form_fields():
     # int (1 - x)^2 over the unit cube = 1/3
     assert abs(lq ** 2 - (1.0 / 3.0) / (2.0 * mu)) <= 1e-13
 
+
+
+def test_decoupled_block_is_indefinite_on_the_columns_problem():
+    """Sec. 3: a_tr is not positive semi-definite.  On the paper's columns problem (free-slip
+    faces) its constrained velocity block has negative eigenvalues - the planar dilation
+    (x, y, 0) has zero a_tr energy and satisfies the free-slip conditions inside a column
+    that touches the faces x = 0 and y = 0 - while the strain and gradient blocks are
+    positive definite."""
+    from oracle.forms import masked
+    p = W.viscosity_columns(8, 4)
+    d = Discretisation(8, p.cell_mu().ravel(), p.face)
+    free = np.flatnonzero(~d.constrained()[: 3 * d.nn])
+    low = {}
+    for form in ("tr", "sym", "grad"):
+        A = d.velocity_block(form)[free][:, free].toarray()
+        s = 1.0 / np.sqrt(np.diag(A))
+        low[form] = np.linalg.eigvalsh(s[:, None] * A * s[None, :])[:5]
+    assert np.count_nonzero(low["tr"] < -1e-3) == 4, low["tr"]
+    assert low["sym"][0] > 1e-2 and low["grad"][0] > 1e-2, (low["sym"], low["grad"])
+    X = _field(d, lambda x, y, z: (x, y, 0.0 * x))
+    assert abs(X @ (d.velocity_block("tr") @ X)) <= 1e-13 * np.abs(X @ (d.velocity_block("sym") @ X))
