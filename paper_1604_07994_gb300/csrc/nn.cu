@@ -73,6 +73,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* er
     }
     return true;
 }
+// After a wait gave up: wait once more, again bounded, for the last of the `issued` commits
+// (alternating between the two barriers) so that no MMA issued by this block is still writing
+// tensor memory when the block frees it.  Each buffer's previous commit had completed before the
+// next one was issued, so the last commit's phase is the only one outstanding on its barrier,
+// and it covers every earlier MMA.  The error flag was set by the wait that gave up.
+__device__ __forceinline__ void drain_commits(uint64_t* bars, int issued) {
+    if (issued > 0) {
+        const int last = issued - 1;
+        mbar_wait(smem_u32(&bars[last & 1]), (last >> 1) & 1, nullptr);
+    }
+}
 __device__ __forceinline__ void fence_async_smem() {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -173,6 +184,7 @@ __global__ void __launch_bounds__(128) k_conv_fwd(ConvArgs a) {
     tc_fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
+    int issued = 0;  // commits issued (block-uniform)
     for (int t = 0; t < 27; ++t) {
         const int buf = t & 1;
         if (t >= 2) ok = mbar_wait(smem_u32(&bars[buf]), ((t >> 1) - 1) & 1, a.err);
@@ -211,10 +223,12 @@ __global__ void __launch_bounds__(128) k_conv_fwd(ConvArgs a) {
                          (t | s) != 0);
             mma_commit(smem_u32(&bars[buf]));
         }
+        ++issued;
     }
     // the last commit (tap 26, buffer 0, its 14th use) covers every MMA issued before it
     if (ok) ok = mbar_wait(smem_u32(&bars[0]), 13 & 1, a.err);
     ok = __syncthreads_and(ok);
+    if (!ok) drain_commits(bars, issued);
     tc_fence_after();
     if (ok) {
         const int r = warp * 32 + (tid & 31);
@@ -295,6 +309,7 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a) {
     tc_fence_after();
     const uint32_t tmem = tslot;
     bool ok = true;
+    int issued = 0;  // commits issued (block-uniform)
     for (int ch = 0; ch < nchunks; ++ch) {
         const int buf = ch & 1;
         if (ch >= 2) ok = mbar_wait(smem_u32(&bars[buf]), ((ch >> 1) - 1) & 1, a.err);
@@ -349,12 +364,14 @@ __global__ void __launch_bounds__(128) k_conv_wgrad(WgradArgs a) {
                          (ch | s) != 0);
             mma_commit(smem_u32(&bars[buf]));
         }
+        ++issued;
     }
     if (ok) {
         const int last = nchunks - 1;
         ok = mbar_wait(smem_u32(&bars[last & 1]), (last >> 1) & 1, a.err);
     }
     ok = __syncthreads_and(ok);
+    if (!ok) drain_commits(bars, issued);
     tc_fence_after();
     if (ok) {
         const int r = warp * 32 + (tid & 31);
