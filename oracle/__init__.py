@@ -16,8 +16,11 @@ It follows the paper (Huber, Ruede, Waluga, Wohlmuth, arXiv:1604.07994) directly
 * ``transfer`` - nested P1 prolongation / restriction between uniformly refined levels
 * ``solvers``  - sparse direct solve, the Uzawa smoother (eq. Uzawa_smooth) and the
                  variable V-cycle of Sec. 5
+* ``nn``       - the learned-initial-guess network (no counterpart in the paper): 3x3x3
+                 convolutions, pooling, up-sampling, loss, backward pass and Adam
 
 Every function is pinned by ``tests/test_oracle_*.py`` against closed forms, the paper's
-lemmas and identities, and convergence to exact solutions; see each docstring for the
-passage it follows.
+lemmas and identities, convergence to exact solutions, and the values the paper prints (the
+relative differences of the layers and columns tables in Sec. 4.2.3-4.2.4, the V-cycle rates
+of Sec. 5; ``tests/golden/``); see each docstring for the passage it follows.
 """
