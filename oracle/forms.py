@@ -161,6 +161,16 @@ class Discretisation:
         q = np.sqrt(p @ (self.mass_matrix(1.0 / (2.0 * self.mu_T)) @ p))
         return np.array([l2, en, q])
 
+    def divergence_weights(self) -> np.ndarray:
+        """D_b = mu_b / m_b with m_b the lumped mass and mu_b m_b = sum_{T ni b} mu_T |T| / 4, so
+        that (B u)^T diag(D) (B v) is the mass-lumped (mu div u, div v): with b(v, q) = -(div v, q)
+        (Sec. 1), (B u)_b = -int div(u) lambda_b ~ -m_b (div u)_b.  Used by the coarse-grid
+        right-hand-side correction of Sec. 5 (A_tr ~ A_sym - B^T diag(D) B)."""
+        mum = np.zeros(self.nn)
+        np.add.at(mum, self.tets.ravel(), np.repeat(self.mu_T * self.vol / 4.0, 4))
+        m = self.lumped_mass()
+        return mum / (m * m)
+
     def pressure_weights(self) -> np.ndarray:
         """w_b = int lambda_b / mu = sum_{T ni b} |T| / (4 mu_T): the discrete form of the
         constraint int mu^{-1} q = 0 that fixes the pressure constant (Sec. 1, space Q)."""

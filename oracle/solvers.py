@@ -26,8 +26,15 @@ Readings of points the paper leaves open (each one is also listed in the design 
 * with no traction face the pressure constant is fixed by the border row
   sum_b w_b p_b = 0, w_b = int lambda_b / mu (the discrete form of int q/mu = 0).
 * coarse levels may use the strain form a_sym instead of a_tr (Sec. 5 swaps a_tr for a_sym
-  on the coarsest grid; here the swap can cover every level below the finest).  The swapped
+  on the coarsest grid; here the swap can cover every level below the finest).  That swapped
   cycle is only used as a preconditioner, so no right-hand-side correction is applied.
+* alternatively (coarse_correction=True) only the coarsest level takes a_sym, with the
+  momentum right-hand side corrected as Sec. 5 describes so that the a_sym system approximates
+  the a_tr one.  Sign and weight follow from the saddle matrix of Sec. 5: lumping the
+  divergence, (mu div u, div v) ~ (B u)^T D (B v), D = diag(mu_b / m_b), hence
+  A_tr ~ A_sym - B^T D B, and with B z = r2 + C q the a_sym system takes r1 + B^T D r2 (the term
+  B^T D C q is dropped).  The paper prints the correction with the opposite sign and without
+  mu; the form above is the one the consistency argument gives.
 * outer iteration: either plain repeated V-cycles (Sec. 5) or flexible GMRES(m)
   (Saad 1993), right-preconditioned by one V-cycle with zero initial guess.  GMRES is an
   addition of this implementation: with a floating stiff inclusion the a_tr Schur
@@ -166,13 +173,19 @@ class Level:
 class Hierarchy:
     """Levels n, n/2, ..., n_coarse of one problem with rediscretised operators."""
 
-    def __init__(self, n, n_coarse, cell_mu, face, form="tr", beta=PSPG_BETA, coarse_form=None):
+    def __init__(self, n, n_coarse, cell_mu, face, form="tr", beta=PSPG_BETA, coarse_form=None,
+                 coarse_correction=False):
+        if coarse_correction and (form != "tr" or coarse_form is not None or n == n_coarse):
+            raise ValueError("coarse_correction swaps a_tr for a_sym on the coarsest level only")
         self.levels = []
         self.P = []
+        self.correction = None
         mu = np.asarray(cell_mu, dtype=np.float64).ravel()
         m = n
         while True:
             lf = form if (m == n or coarse_form is None) else coarse_form
+            if coarse_correction and m == n_coarse:
+                lf = "sym"
             self.levels.append(Level(m, mu, face, lf, beta))
             if m == n_coarse:
                 break
@@ -183,12 +196,27 @@ class Hierarchy:
         for l in range(len(self.levels) - 1):
             f, c = self.levels[l], self.levels[l + 1]
             self.P.append(system_prolongation(c.n, f.con, c.con))
+        if coarse_correction:
+            self.correction = self.levels[-1].disc.divergence_weights()
+
+    def coarse_rhs(self, b):
+        """Right-hand side of the coarsest solve: b itself, or with coarse_correction the
+        momentum rows r1 + B^T D r2 of the a_sym swap (Sec. 5; sign and weight as derived in the
+        module notes), constrained rows zero."""
+        if self.correction is None:
+            return b
+        L = self.levels[-1]
+        nn = L.nn
+        out = b.copy()
+        out[: 3 * nn] += L.BT @ (self.correction * b[3 * nn:])
+        out[L.con] = 0.0
+        return out
 
     def vcycle(self, x, b, l=0):
         """Variable V-cycle on level l, x updated in place and returned."""
         L = self.levels[l]
         if l == len(self.levels) - 1:
-            x[:] = L.direct(b)
+            x[:] = L.direct(self.coarse_rhs(b))
             return x
         nu = 3 + 2 * l
         for _ in range(nu):

@@ -291,3 +291,20 @@ def test_decoupled_block_is_indefinite_on_the_columns_problem():
     assert low["sym"][0] > 1e-2 and low["grad"][0] > 1e-2, (low["sym"], low["grad"])
     X = _field(d, lambda x, y, z: (x, y, 0.0 * x))
     assert abs(X @ (d.velocity_block("tr") @ X)) <= 1e-13 * np.abs(X @ (d.velocity_block("sym") @ X))
+
+
+def test_divergence_weights_lump_the_div_div_form_exactly_for_constant_divergence():
+    """D_b = mu_b / m_b makes (B u)^T diag(D) (B u) the mass-lumped (mu div u, div u); for a
+    field of constant divergence the lumping is exact: (B u)_b = -div(u) m_b, so the sum is
+    div^2 sum_T mu_T |T| = div^2 sum_i mu_i |Omega_i| (piecewise mu)."""
+    n = 4
+    mu = _random_piecewise_mu(n, 6, lattice=2)
+    d = _disc(n, mu)
+    B = d.divergence()
+    D = d.divergence_weights()
+    s = np.sum(mu) / n ** 3
+    for field, div in ((lambda x, y, z: (x, y, z), 3.0), (lambda x, y, z: (x, 0.0 * x, 0.0 * x), 1.0),
+                       (lambda x, y, z: (0.0 * x, 2.0 * y, -z), 1.0)):
+        Bu = B @ _field(d, field)
+        assert np.allclose(Bu, -div * d.lumped_mass(), rtol=1e-12, atol=1e-15)
+        assert abs(Bu @ (D * Bu) - div ** 2 * s) <= 1e-12 * div ** 2 * s
