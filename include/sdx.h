@@ -104,7 +104,8 @@ typedef struct {
  * grid or a coarsest grid too large, SDX_ENOMEM, SDX_ESINGULAR, SDX_ECUDA.  On error *out is set to NULL. */
 int sdx_create(const sdx_desc* desc, sdx_hier_t* out);
 
-/* Release every buffer of the hierarchy.  Synchronises the device first.  NULL is a no-op. */
+/* Release every buffer of the hierarchy.  Synchronises the device first.  NULL is a no-op.
+ * A hierarchy obtained from sdx_batch_instance is refused with SDX_EINVAL (the batch owns it). */
 int sdx_destroy(sdx_hier_t h);
 
 /* Number of levels, and nodes / free DoFs of one level (0 = finest). */

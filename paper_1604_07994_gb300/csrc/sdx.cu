@@ -701,7 +701,12 @@ int sdx_create(const sdx_desc* desc, sdx_hier_t* out) {
 }
 
 int sdx_destroy(sdx_hier_t h) {
-    hier_free(as_hier(h));
+    Hier* H = as_hier(h);
+    if (H && H->released) {  // an instance handle of a batch: the batch frees it
+        set_error("this hierarchy belongs to a batch: sdx_batch_destroy frees it");
+        return SDX_EINVAL;
+    }
+    hier_free(H);
     return SDX_OK;
 }
 

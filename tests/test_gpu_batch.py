@@ -186,3 +186,18 @@ def test_batch_statuses_are_per_instance(sdx):
     st = B.sdx_batch_solve(bs, xs, rtol=1e-10, maxit=100, allow_codes=(sdx.ENONFINITE,))
     assert st[0]["status"] == sdx.ENONFINITE
     assert st[1]["status"] == 0 and st[1]["res"] <= 1e-10 * st[1]["bnorm"]
+
+
+def test_destroy_refuses_a_batch_owned_hierarchy(sdx):
+    """sdx_destroy on an instance handle of a batch returns SDX_EINVAL instead of freeing what
+    the batch still owns; the batch and its instance stay usable."""
+    probs = [W.cube_inclusion(8, 4)]
+    B = sdx.Batch(probs, prec=1, autotune=False)
+    H = B.instance(0)
+    assert sdx.load().sdx_destroy(H._h) == sdx.EINVAL
+    assert "batch" in sdx.load().sdx_last_error().decode()
+    b, _ = _rhs(probs[0])
+    x = _dev(np.zeros_like(b))
+    st = B.sdx_batch_solve([_dev(b)], [x], rtol=1e-8, maxit=100)
+    assert st[0]["res"] <= 1e-8 * st[0]["bnorm"]
+    B.close()
