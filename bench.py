@@ -326,6 +326,15 @@ def _time(fn, reps, stream, torch):
     return e0.elapsed_time(e1) / reps
 
 
+def _guarded(block):
+    """Run one supplementary measurement block; a failure is reported in its place (with the
+    exception) instead of taking the benchmark line, measured before it, down with it."""
+    try:
+        return block()
+    except Exception as e:  # noqa: BLE001 - reported in the output line
+        return {"error": repr(e)}
+
+
 def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
     out = {}
     n = prob.n
@@ -396,15 +405,15 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
             H2.close()
         out["variants"] = var
     if not args.no_layer:
-        out["top_layer_256"] = run_layer(args, sdx, torch, W, stream)
+        out["top_layer_256"] = _guarded(lambda: run_layer(args, sdx, torch, W, stream))
     if not args.no_batch:
-        out["batched_48"] = run_batch(args, sdx, torch)
+        out["batched_48"] = _guarded(lambda: run_batch(args, sdx, torch))
     if not args.no_guess:
-        out["learned_guess"] = run_guess(args, sdx, torch)
+        out["learned_guess"] = _guarded(lambda: run_guess(args, sdx, torch))
     if not args.no_paper:
-        out["paper_columns"] = run_paper(args, sdx, torch)
+        out["paper_columns"] = _guarded(lambda: run_paper(args, sdx, torch))
     if not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1:
-        out["cpu_baseline"] = oracle_sample()
+        out["cpu_baseline"] = _guarded(oracle_sample)
     return out
 
 
