@@ -28,6 +28,8 @@ Readings of points the paper leaves open (each one is also listed in the design 
 * coarse levels may use the strain form a_sym instead of a_tr (Sec. 5 swaps a_tr for a_sym
   on the coarsest grid; here the swap can cover every level below the finest).  That swapped
   cycle is only used as a preconditioner, so no right-hand-side correction is applied.
+* the coarsest solve is direct, or (coarse_solver="minres") the block-preconditioned MINRES
+  iteration of Sec. 5 (block_minres) stopped at a relative tolerance.
 * alternatively (coarse_correction=True) only the coarsest level takes a_sym, with the
   momentum right-hand side corrected as Sec. 5 describes so that the a_sym system approximates
   the a_tr one.  Sign and weight follow from the saddle matrix of Sec. 5: lumping the
@@ -174,9 +176,12 @@ class Hierarchy:
     """Levels n, n/2, ..., n_coarse of one problem with rediscretised operators."""
 
     def __init__(self, n, n_coarse, cell_mu, face, form="tr", beta=PSPG_BETA, coarse_form=None,
-                 coarse_correction=False):
+                 coarse_correction=False, coarse_solver="direct", coarse_rtol=1e-8):
         if coarse_correction and (form != "tr" or coarse_form is not None or n == n_coarse):
             raise ValueError("coarse_correction swaps a_tr for a_sym on the coarsest level only")
+        if coarse_solver not in ("direct", "minres"):
+            raise ValueError("coarse_solver is 'direct' or 'minres'")
+        self.coarse_solver, self.coarse_rtol = coarse_solver, coarse_rtol
         self.levels = []
         self.P = []
         self.correction = None
@@ -216,7 +221,11 @@ class Hierarchy:
         """Variable V-cycle on level l, x updated in place and returned."""
         L = self.levels[l]
         if l == len(self.levels) - 1:
-            x[:] = L.direct(self.coarse_rhs(b))
+            rhs = self.coarse_rhs(b)
+            if self.coarse_solver == "minres":
+                x[:] = block_minres(L, rhs, rtol=self.coarse_rtol)
+            else:
+                x[:] = L.direct(rhs)
             return x
         nu = 3 + 2 * l
         for _ in range(nu):
@@ -242,6 +251,48 @@ class Hierarchy:
             self.vcycle(x, b)
             hist.append(np.linalg.norm(L.residual(x, b)[L.free]))
         return x, np.array(hist)
+
+
+def block_minres(L, b, rtol=1e-10, maxit=1000, inner_rtol=1e-12):
+    """The coarse-grid solver of Sec. 5: MINRES on the level's saddle system (free DoFs),
+    preconditioned block-diagonally by the velocity block A, applied through a
+    Jacobi-preconditioned CG iteration, and the lumped pressure mass matrix.  The pressure
+    mass is weighted by 1/mu (w_b = int lambda_b / mu, the Schur complement of a variable
+    viscosity scaling like that); MINRES needs the preconditioner symmetric positive
+    definite, which holds for a_sym and the gradient form but not for a_tr (Sec. 5 swaps the
+    form for this reason).  Scipy's MINRES and CG serve as the two iterations.  With a pressure
+    null space the result is shifted to sum_b w_b p_b = 0.  Returns the full-size solution."""
+    free = np.flatnonzero(L.free)
+    nn = L.nn
+    Kff = L.K[free][:, free].tocsr()
+    nu = int(np.count_nonzero(free < 3 * nn))
+    A = Kff[:nu, :nu].tocsr()
+    dA = A.diagonal()
+    w = L.disc.pressure_weights()
+    wp = w[free[nu:] - 3 * nn]
+
+    def apply_prec(r):
+        z = np.empty_like(r)
+        zu, info = spla.cg(A, r[:nu], rtol=inner_rtol, atol=0.0, maxiter=10 * nu,
+                           M=spla.LinearOperator(A.shape, matvec=lambda v: v / dA))
+        if info != 0:
+            raise RuntimeError("inner CG did not converge (velocity block not positive definite?)")
+        z[:nu] = zu
+        z[nu:] = r[nu:] / wp
+        return z
+
+    M = spla.LinearOperator(Kff.shape, matvec=apply_prec)
+    try:
+        sol, info = spla.minres(Kff, b[free], M=M, rtol=rtol, maxiter=maxit)
+    except ValueError as e:  # scipy's check that the preconditioned operator is symmetric
+        raise RuntimeError(f"MINRES cannot run with this preconditioner: {e}") from e
+    if info != 0:
+        raise RuntimeError(f"MINRES did not converge (info {info})")
+    x = np.zeros(4 * nn)
+    x[free] = sol
+    if L.nullspace:
+        x[3 * nn:] -= np.dot(w, x[3 * nn:]) / w.sum()
+    return x
 
 
 def fgmres(K, precond, b, free, rtol=1e-8, restart=30, maxit=200, x0=None):
