@@ -48,6 +48,8 @@ def parse():
                          "guess: only the learned-initial-guess experiment; batch: only the batched workload")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="arithmetic of --mode sweep")
     ap.add_argument("--form", default="tr", choices=["tr", "sym", "grad"])
+    ap.add_argument("--beta", type=float, default=1.0 / 12.0,
+                    help="pressure-stabilisation constant of the three-box workload (tau = beta h^2 / mu)")
     ap.add_argument("--maxit", type=int, default=500,
                     help="iteration cap per solve (profiling runs use a small cap)")
     ap.add_argument("--no-details", action="store_true", help="skip sweeps, e2e, variants, CPU leg")
@@ -233,7 +235,7 @@ def main():
     t0 = time.perf_counter()
     # decoupled operator a_tr on the finest level; the coarser levels use a_sym (the coarse-grid
     # swap of Sec. 5 extended to every coarse level), FP64 throughout
-    H = sdx.Hierarchy.from_problem(prob, form="tr", coarse_form="sym", prec=sdx.PREC_FP64)
+    H = sdx.Hierarchy.from_problem(prob, form="tr", coarse_form="sym", prec=sdx.PREC_FP64, beta=args.beta)
     setup_s = time.perf_counter() - t0
     _, nodes, free = H.sdx_level_size(0)
     f = torch.from_numpy(prob.nodal_forcing().ravel()).to(dev)
@@ -303,7 +305,7 @@ def main():
         "config": {"workload": f"three_boxes_{n}: {n}^3 cells ({free} free DoF), 3 seeded boxes on the 1/8 lattice, mu ratio 1e4, no-slip walls, manufactured forcing",
                    "form": "decoupled (a_tr with interface strain rows) on the finest level, a_sym on the coarser levels",
                    "solver": f"FGMRES({RESTART}) + V_var(3,3) Uzawa multigrid, 5 levels, coarsest 8^3 dense FP64 inverse",
-                   "rtol": 1e-8, "time_to_1e8_s": ms * 1e-3, "iterations": iters, "final_rel_res": final_res,
+                   "rtol": 1e-8, "pspg_beta": args.beta, "time_to_1e8_s": ms * 1e-3, "iterations": iters, "final_rel_res": final_res,
                    "setup_s": setup_s, "l2": "inputs larger than L2 (each 4-component FP64 vector is 69 MB; solver working set > 4 GB)",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
         "gpu_launches": int(launches),
@@ -386,7 +388,7 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
                                         ("decoupled_fp32_refined", "tr", sdx.PREC_FP32_REFINED, "sym"),
                                         ("strain_fp32_refined", "sym", sdx.PREC_FP32_REFINED, None),
                                         ("decoupled_tr_coarse_fp32_refined", "tr", sdx.PREC_FP32_REFINED, None)):
-            H2 = sdx.Hierarchy.from_problem(prob, form=form, prec=prec, coarse_form=cform)
+            H2 = sdx.Hierarchy.from_problem(prob, form=form, prec=prec, coarse_form=cform, beta=args.beta)
             x2 = torch.zeros_like(b)
             st = H2.sdx_solve(b, x2, rtol=1e-8, maxit=500, outer=sdx.OUTER_FGMRES, restart=30)
             reps2 = 2
@@ -787,7 +789,7 @@ def run_sweeps(args):
     torch.cuda.set_device(0)
     prob = W.three_boxes(args.n, 8, contrast=1e4)
     prec = sdx.PREC_FP64 if args.prec == "fp64" else sdx.PREC_FP32_REFINED
-    H = sdx.Hierarchy.from_problem(prob, form=args.form, prec=prec)
+    H = sdx.Hierarchy.from_problem(prob, form=args.form, prec=prec, beta=args.beta)
     _, nn, free = H.sdx_level_size(0)
     dt = torch.float64 if args.prec == "fp64" else torch.float32
     con = torch.from_numpy(H.sdx_constraint_mask(0)).cuda()
