@@ -26,6 +26,11 @@
  *
  * Every function returns SDX_OK (0) or a negative error code; sdx_last_error() gives a
  * message for the calling thread's last failure.  No C++ exception crosses this interface.
+ * Errors common to the entry points below, checked before anything is launched: SDX_EINVAL
+ * for a NULL handle or vector, a level outside 0..levels-1, or (for the smoothers, cycles and
+ * solves) a hierarchy owned by a batch; SDX_ECUDA when a CUDA runtime call fails.  The
+ * library cannot see the extent of a vector pointer: a vector shorter than its level's
+ * 4*(n+1)^3 entries (3*(n+1)^3 for nodal forcing) is undefined behaviour.
  */
 #ifndef SDX_H
 #define SDX_H
