@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 from typing import Optional, Sequence
 
 import numpy as np
@@ -61,13 +62,19 @@ class sdx_stats(ctypes.Structure):
 
 
 _lib = None
+_load_lock = threading.Lock()
 
 
 def load() -> ctypes.CDLL:
-    """Load libsdx.so (once).  Raises if it has not been built."""
-    global _lib
+    """Load libsdx.so (once, thread-safe).  Raises if it has not been built."""
     if _lib is not None:
         return _lib
+    with _load_lock:
+        return _lib if _lib is not None else _load_locked()
+
+
+def _load_locked() -> ctypes.CDLL:
+    global _lib
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_1604_07994_gb300.build.build()")
     lib = ctypes.CDLL(LIB_PATH)
