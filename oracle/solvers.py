@@ -142,23 +142,32 @@ class Level:
         return x
 
     # ------------------------------------------------------------------ smoother
+    def velocity_pass(self, u, p, f, red):
+        """One colour of the velocity Gauss-Seidel on A u = f - B^T p, in place on u: every
+        free component of every node of the colour (red: i+j+k even) takes
+        u += (f - B^T p - A u) / diag(A), all from the residual before the pass."""
+        nn = self.nn
+        r = f - self.BT @ p - self.A @ u
+        sel = np.tile(self.red if red else ~self.red, 3) & self.free[: 3 * nn]
+        u[sel] += r[sel] / self.diagA[sel]
+
+    def pressure_pass(self, u, p, g, red):
+        """One colour of the relaxed pressure Gauss-Seidel on C p = B u - g, in place on p:
+        p += omega (B u - C p - g) / diag(C) at the nodes of the colour."""
+        s = (self.B @ u - g) - self.C @ p
+        sel = self.red if red else ~self.red
+        p[sel] += OMEGA * s[sel] / self.diagC[sel]
+
     def velocity_sweep(self, u, p, f):
         """Symmetric hybrid red-black Gauss-Seidel for A u = f - B^T p: colours R, B, R,
         all free components of the colour updated from the same residual."""
-        nn = self.nn
-        rhs = f - self.BT @ p
         for red in (True, False, True):
-            r = rhs - self.A @ u
-            sel = np.tile(self.red if red else ~self.red, 3) & self.free[: 3 * nn]
-            u[sel] += r[sel] / self.diagA[sel]
+            self.velocity_pass(u, p, f, red)
 
     def pressure_sweep(self, u, p, g):
         """Forward red-black Gauss-Seidel on C p = B u - g with relaxation omega."""
-        bu = self.B @ u - g
         for red in (True, False):
-            s = bu - self.C @ p
-            sel = self.red if red else ~self.red
-            p[sel] += OMEGA * s[sel] / self.diagC[sel]
+            self.pressure_pass(u, p, g, red)
 
     def uzawa(self, x, b):
         """One Uzawa smoothing step (eq. Uzawa_smooth) on x = (u, p) in place."""

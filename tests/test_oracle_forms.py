@@ -201,6 +201,26 @@ def test_divergence_and_stabilisation_consistency():
         assert np.abs(bt1[free]).max() <= 1e-15
 
 
+@pytest.mark.parametrize("n,seed", [(4, 21), (6, 22), (8, 23)])
+def test_stabilisation_energy_of_linear_pressure_closed_form(n, seed):
+    """For a linear pressure q = a + g.x the gradient is exact and constant, so
+    q^T C q = sum_T tau_T |T| |g|^2 = |g|^2 beta h^2 sum_cells h^3 / mu_cell
+    (six tetrahedra of volume h^3/6 per cell, tau_T = beta h^2 / mu_T).  With a viscosity that
+    varies cell by cell this pins the power of h and of mu in tau_T and the volume factor |T|,
+    which C 1 = 0 cannot see (a wrong exponent or a missing |T| keeps C 1 = 0)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    mu = _random_piecewise_mu(n, seed)
+    d = _disc(n, mu)
+    g = rng.normal(size=3)
+    x = d.xyz
+    q = 0.7 + x @ g
+    exact = float(g @ g) * d.beta * d.h ** 2 * np.sum(d.h ** 3 / mu)
+    assert abs(q @ (d.stabilisation() @ q) - exact) <= 1e-13 * exact
+    # the same energy with beta doubled: C is linear in beta
+    d2 = Discretisation(n, mu, (DIRICHLET,) * 6, beta=2.0 * d.beta)
+    assert abs(q @ (d2.stabilisation() @ q) - 2.0 * exact) <= 1e-13 * exact
+
+
 def test_mass_and_pressure_weights():
     p = W.three_boxes(8, 8, contrast=1e4)
     d = Discretisation(8, p.cell_mu().ravel(), p.face)
