@@ -158,6 +158,13 @@ int sdx_apply_f32(sdx_hier_t h, int level, const float* x, float* y, void* strea
 int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const float* b, float* x,
                         void* stream);
 
+/* `steps` FP32 Uzawa smoothing steps (as sdx_uzawa, 1 <= steps <= 1000) on one level, in place
+ * on the FP32 vector x, with exactly the launches the FP32 V-cycle uses on that level: on levels
+ * of at most 10000 nodes all steps run in one thread-block cluster (hardware cluster barriers
+ * between the colour passes), elsewhere one launch per pass.  Needs a hierarchy created with
+ * prec = SDX_PREC_FP32_REFINED.  Paper: Sec. 5, eq. (Uzawa_smooth). */
+int sdx_uzawa_f32(sdx_hier_t h, int level, const float* b, float* x, int steps, void* stream);
+
 /* Allocation-free variant of the velocity pass of sdx_smooth_pass (which = 0), FP64.
  * The paper has no counterpart; this exists for callers that cannot allocate device memory at
  * the point of the call - for example code running in a phase where cudaMalloc is forbidden
@@ -172,7 +179,10 @@ int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const fl
  *   - A level whose colour has more than SDX_NOALLOC_MAX_ROWS boundary/interface rows is
  *     rejected with SDX_EINVAL before anything is launched (see sdx_last_error()).
  *   - The first call on a device looks up the array's device address (once per device, with
- *     that device current); make that first call before any stream capture.
+ *     that device current); make that first call before any stream capture.  The address is
+ *     kept for the life of the process: after cudaDeviceReset (or anything else that destroys
+ *     and recreates the device's primary context) the kept address is stale, so do not call
+ *     this entry point again in that process.
  *   - All calls share the one array.  Nothing in it needs to start at zero (each call writes
  *     every entry it later reads), but calls whose executions overlap on the GPU (different
  *     streams, different hierarchies) race on it: serialise them. */

@@ -830,6 +830,19 @@ int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const fl
     API_END
 }
 
+int sdx_uzawa_f32(sdx_hier_t h, int level, const float* b, float* x, int steps, void* stream) {
+    Hier* H = as_hier(h);
+    int c = check_work(H, level);
+    if (c) return c;
+    if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
+    if (steps < 1 || steps > 1000) { set_error("steps must be in 1..1000"); return SDX_EINVAL; }
+    if (H->prec != SDX_PREC_FP32_REFINED) { set_error("hierarchy was not created for FP32"); return SDX_EINVAL; }
+    API_BEGIN
+    launch_uzawa_steps<float>(*H, level, x, b, steps, (cudaStream_t)stream);
+    return launched("sdx_uzawa_f32");
+    API_END
+}
+
 int sdx_smooth_pass_noalloc(sdx_hier_t h, int level, int colour, const double* b, double* x,
                             void* stream) {
     Hier* H = as_hier(h);
@@ -837,11 +850,13 @@ int sdx_smooth_pass_noalloc(sdx_hier_t h, int level, int colour, const double* b
     if (c) return c;
     if (!x || !b) { set_error("null vector"); return SDX_EINVAL; }
     if (colour != 0 && colour != 1) { set_error("colour must be 0 or 1"); return SDX_EINVAL; }
+    API_BEGIN
     std::string err;
     const int rc = launch_velocity_pass_noalloc(*H, level, colour, x, b, (cudaStream_t)stream, err);
     if (rc == -1) { set_error(err); return SDX_EINVAL; }
     if (rc == -2) { set_error(err); return SDX_ECUDA; }
     return launched("sdx_smooth_pass_noalloc");
+    API_END
 }
 
 int sdx_restrict(sdx_hier_t h, int level, const double* rf, double* bc, void* stream) {

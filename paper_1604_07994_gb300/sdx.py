@@ -32,6 +32,7 @@ NOALLOC_MAX_ROWS = 65536
 EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_constraint_mask",
             "sdx_interface_mask", "sdx_apply", "sdx_residual", "sdx_rhs", "sdx_uzawa", "sdx_smooth_pass",
             "sdx_kernel_launches", "sdx_smooth_pass_noalloc", "sdx_apply_f32", "sdx_smooth_pass_f32",
+            "sdx_uzawa_f32",
             "sdx_restrict", "sdx_prolong_add", "sdx_vcycle", "sdx_solve", "sdx_solve_host",
             "sdx_batch_create", "sdx_batch_destroy", "sdx_batch_size", "sdx_batch_shape", "sdx_batch_instance",
             "sdx_batch_vcycle", "sdx_batch_solve", "sdx_net_param_count", "sdx_net_create",
@@ -94,6 +95,7 @@ def _load_locked() -> ctypes.CDLL:
         "sdx_smooth_pass_noalloc": [P, I, I, P, P, P],
         "sdx_apply_f32": [P, I, P, P, P],
         "sdx_smooth_pass_f32": [P, I, I, I, P, P, P],
+        "sdx_uzawa_f32": [P, I, P, P, I, P],
         "sdx_restrict": [P, I, P, P, P],
         "sdx_prolong_add": [P, I, P, P, P],
         "sdx_vcycle": [P, P, P, P],
@@ -297,6 +299,11 @@ class Hierarchy:
         m = self._len(level)
         pb, px = _vecs((b, m), (x, m), itemsize=4)
         _check(load().sdx_smooth_pass_f32(self._h, level, which, colour, pb, px, _stream(stream)))
+
+    def sdx_uzawa_f32(self, level, b, x, steps=1, stream=None):
+        m = self._len(level)
+        pb, px = _vecs((b, m), (x, m), itemsize=4)
+        _check(load().sdx_uzawa_f32(self._h, level, pb, px, int(steps), _stream(stream)))
 
     def sdx_smooth_pass_noalloc(self, level, colour, b, x, stream=None):
         m = self._len(level)
