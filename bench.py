@@ -43,11 +43,13 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per side (workload size)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "guess", "batch", "paper", "conv"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "levels", "guess", "batch", "paper", "conv"],
                     help="sweep: only time the operator apply and smoother passes (profiling); "
                          "guess: only the learned-initial-guess experiment; batch: only the batched workload")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="arithmetic of --mode sweep")
     ap.add_argument("--form", default="tr", choices=["tr", "sym", "grad"])
+    ap.add_argument("--coarse-form", default="sym", choices=["tr", "sym", "grad"],
+                    help="form of the coarser levels in --mode levels")
     ap.add_argument("--beta", type=float, default=1.0 / 12.0,
                     help="pressure-stabilisation constant of the three-box workload (tau = beta h^2 / mu)")
     ap.add_argument("--maxit", type=int, default=500,
@@ -211,6 +213,9 @@ def main():
         return
     if args.mode == "sweep":
         run_sweeps(args)
+        return
+    if args.mode == "levels":
+        run_levels(args)
         return
     if args.mode in ("guess", "batch", "paper", "conv"):
         import torch
@@ -778,6 +783,73 @@ def run_guess(args, sdx, torch):
         out[f"iterations_{key}_mean"] = float(np.mean([e[key]["iterations"] for e in ev]))
         out[f"wall_time_saved_frac_{key}"] = (z - sum(e[key]["seconds"] for e in ev)) / z
     return out
+
+
+def level_times(H, sdx, torch, stream, prec="fp64", reps=20):
+    """CUDA-event times of the pieces of one V_var cycle on every level of a hierarchy: one
+    Uzawa step (nu = 3 + 2l of them pre and post), the residual, restriction, prolongation, and
+    the cycle time they add up to on that level (launched one call at a time, so each piece
+    also carries its launch latency; inside the captured cycle the same kernels run back to
+    back)."""
+    nl = H.sdx_levels()
+    dt = torch.float64 if prec == "fp64" else torch.float32
+    out = []
+    vecs = []
+    for l in range(nl):
+        _, nodes, free = H.sdx_level_size(l)
+        x = torch.zeros(4 * nodes, dtype=dt, device="cuda")
+        b = torch.zeros(4 * nodes, dtype=dt, device="cuda")
+        vecs.append((x, b, nodes, free))
+    for l in range(nl):
+        x, b, nodes, free = vecs[l]
+        row = {"level": l, "nodes": nodes, "free_dofs": free}
+        if l == nl - 1:
+            out.append(row)
+            continue
+        nu = 3 + 2 * l
+        if prec == "fp64":
+            t_uz = _time(lambda: H.sdx_uzawa(l, b, x), reps, stream, torch)
+            r = torch.empty_like(x)
+            t_res = _time(lambda: H.sdx_residual(l, b, x, r), reps, stream, torch)
+            bc = vecs[l + 1][1]
+            t_rs = _time(lambda: H.sdx_restrict(l, r, bc), reps, stream, torch)
+            t_pr = _time(lambda: H.sdx_prolong_add(l, vecs[l + 1][0], x), reps, stream, torch)
+            row.update({"uzawa_step_ms": t_uz, "residual_ms": t_res, "restrict_ms": t_rs, "prolong_ms": t_pr,
+                        "nu": nu, "level_cycle_ms": 2 * nu * t_uz + t_res + t_rs + t_pr})
+        else:
+            t_st = _time(lambda: H.sdx_uzawa_f32(l, b, x, nu), reps, stream, torch)
+            y = torch.empty_like(x)
+            t_ap = _time(lambda: H.sdx_apply_f32(l, x, y), reps, stream, torch)
+            row.update({"nu_steps_ms": t_st, "apply_ms": t_ap, "nu": nu,
+                        "level_cycle_ms": 2 * t_st + t_ap})
+        out.append(row)
+    return out
+
+
+def run_levels(args):
+    """Per-level times of the V-cycle on the benchmark workload (decoupled form on the finest
+    level, strain form below, as the headline solve), FP64 and FP32, and the whole captured
+    cycle for comparison."""
+    import torch
+    from paper_1604_07994_gb300 import sdx
+    from paper_1604_07994_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    prob = W.three_boxes(args.n, 8, contrast=1e4)
+    stream = torch.cuda.current_stream()
+    res = {"mode": "levels", "n": args.n}
+    for prec, p in (("fp64", sdx.PREC_FP64), ("fp32", sdx.PREC_FP32_REFINED)):
+        H = sdx.Hierarchy.from_problem(prob, form="tr", coarse_form=args.coarse_form, prec=p, beta=args.beta)
+        _, nodes, _ = H.sdx_level_size(0)
+        b = torch.zeros(4 * nodes, dtype=torch.float64, device="cuda")
+        f = torch.from_numpy(prob.nodal_forcing().ravel()).cuda()
+        H.sdx_rhs(f, b)
+        xv = torch.zeros_like(b)
+        t_vc = _time(lambda: H.sdx_vcycle(b, xv), 10, stream, torch)
+        lv = level_times(H, sdx, torch, stream, prec)
+        res[prec] = {"vcycle_ms": t_vc, "levels": lv,
+                     "finest_share": lv[0]["level_cycle_ms"] / max(sum(r.get("level_cycle_ms", 0) for r in lv), 1e-12)}
+        H.close()
+    print(json.dumps(res), flush=True)
 
 
 def run_sweeps(args):

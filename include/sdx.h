@@ -75,8 +75,8 @@ typedef struct sdx_hier* sdx_hier_t; /* opaque, library-owned hierarchy */
 typedef struct {
     int n;                  /* cells per side on the finest grid; n = n_coarse * 2^k, k >= 0,
                                n <= 1024 */
-    int n_coarse;           /* cells per side on the coarsest grid (>= 2); every viscosity
-                               interface must lie on a plane of that grid */
+    int n_coarse;           /* cells per side on the coarsest grid (>= 2); with coarsening = 0
+                               every viscosity interface must lie on a plane of that grid */
     const uint8_t* cell_id; /* HOST array of n^3 subdomain ids, cell (i,j,k) at
                                i + n*(j + n*k); ids must be < n_mu (and < 255) */
     const double* mu;       /* HOST viscosity table indexed by id, all finite and > 0 */
@@ -88,6 +88,23 @@ typedef struct {
     int prec;               /* SDX_PREC_* for sdx_vcycle and sdx_solve */
     double pspg_beta;       /* stabilisation constant beta (> 0); 1/12 is the default used
                                throughout this library's tests */
+    int coarsest_form;      /* SDX_FORM_* on the coarsest level only, or -1 for "same as
+                               coarse_form" (with a single level the finest form applies) */
+    int coarse_correction;  /* 1: the coarse-grid variant of Sec. 5 - the coarsest solve takes
+                               the momentum right-hand side r1 + B^T D r2 (D = diag(mu_b / m_b),
+                               m_b the lumped mass, mu_b its mu-weighted mean) so that its a_sym
+                               system approximates the a_tr one (A_tr ~ A_sym - B^T D B); needs
+                               at least two levels and coarsest_form = SDX_FORM_STRAIN.  The
+                               correction is folded into the coarsest inverse when the hierarchy
+                               is built, so a cycle costs the same.  0: no correction. */
+    int coarsening;         /* how coarse cells get their viscosity id from their 8 children:
+                               0 = every viscosity interface must lie on a plane of the coarsest
+                               grid (the 8 children agree; SDX_EINVAL otherwise); 1 = interfaces
+                               the coarse grids do not resolve (a level set cutting the cells,
+                               Sec. 2.2 closing remark): the id whose viscosity most children
+                               have, a tie going to the larger viscosity (the smallest such id).
+                               The finest operator is exact either way; the coarse levels only
+                               precondition. */
 } sdx_desc;
 
 typedef struct {
@@ -237,7 +254,7 @@ typedef struct sdx_batch* sdx_batch_t; /* opaque, library-owned */
  * concatenated work vectors.  autotune != 0 times candidate block shapes (64..512 threads per
  * block, persistent grids of one or two waves of resident blocks) of the colour-pass and
  * residual launches on every level and keeps the fastest.  Synchronous.  Errors as sdx_create, plus SDX_EINVAL
- * when the descriptors disagree on form, coarse_form or prec.  On error *out is NULL. */
+ * when the descriptors disagree on form, coarse_form, coarsest_form, coarse_correction or prec.  On error *out is NULL. */
 int sdx_batch_create(const sdx_desc* descs, int count, int autotune, sdx_batch_t* out);
 
 /* Release the batch and every hierarchy in it (synchronises the device).  NULL is a no-op. */

@@ -57,17 +57,29 @@ OMEGA = 0.3
 DENSE_LIMIT = 7000
 
 
-def coarsen_cell_mu(n: int, cell_mu: np.ndarray) -> np.ndarray:
-    """Viscosity of the cells of the next coarser grid (each coarse cell is the union of 8
-    fine cells, which must share one viscosity: interfaces resolved on every level)."""
+def coarsen_cell_mu(n: int, cell_mu: np.ndarray, rule: str = "resolved") -> np.ndarray:
+    """Viscosity of the cells of the next coarser grid; each coarse cell is the union of 8 fine
+    cells.  rule "resolved": the 8 must share one viscosity (interfaces resolved on every
+    level).  rule "majority" (interfaces the coarse grids do not resolve, e.g. a level set, Sec.
+    2.2 closing remark): the viscosity that most of the 8 children have, a tie going to the
+    larger viscosity.  The coarse levels only precondition; the finest operator is exact."""
     m = np.asarray(cell_mu).reshape(n, n, n)
     c = m[0::2, 0::2, 0::2]
-    for dk in (0, 1):
-        for dj in (0, 1):
-            for di in (0, 1):
-                if not np.array_equal(m[dk::2, dj::2, di::2], c):
-                    raise ValueError("viscosity interface not resolved on the coarser grid")
-    return np.ascontiguousarray(c).ravel()
+    kids = [m[dk::2, dj::2, di::2] for dk in (0, 1) for dj in (0, 1) for di in (0, 1)]
+    if rule == "resolved":
+        for k in kids:
+            if not np.array_equal(k, c):
+                raise ValueError("viscosity interface not resolved on the coarser grid")
+        return np.ascontiguousarray(c).ravel()
+    if rule != "majority":
+        raise ValueError("rule is 'resolved' or 'majority'")
+    stack = np.stack([k.ravel() for k in kids])          # [8, cells]
+    out = np.empty(stack.shape[1])
+    for cell in range(stack.shape[1]):
+        vals, counts = np.unique(stack[:, cell], return_counts=True)
+        best = counts.max()
+        out[cell] = vals[counts == best].max()
+    return out
 
 
 class Level:
@@ -185,7 +197,8 @@ class Hierarchy:
     """Levels n, n/2, ..., n_coarse of one problem with rediscretised operators."""
 
     def __init__(self, n, n_coarse, cell_mu, face, form="tr", beta=PSPG_BETA, coarse_form=None,
-                 coarse_correction=False, coarse_solver="direct", coarse_rtol=1e-8):
+                 coarse_correction=False, coarse_solver="direct", coarse_rtol=1e-8,
+                 coarsening="resolved"):
         if coarse_correction and (form != "tr" or coarse_form is not None or n == n_coarse):
             raise ValueError("coarse_correction swaps a_tr for a_sym on the coarsest level only")
         if coarse_solver not in ("direct", "minres"):
@@ -205,7 +218,7 @@ class Hierarchy:
                 break
             if m % 2 or m // 2 < n_coarse:
                 raise ValueError("n must be n_coarse * 2^k")
-            mu = coarsen_cell_mu(m, mu)
+            mu = coarsen_cell_mu(m, mu, coarsening)
             m //= 2
         for l in range(len(self.levels) - 1):
             f, c = self.levels[l], self.levels[l + 1]

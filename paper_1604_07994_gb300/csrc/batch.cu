@@ -34,9 +34,10 @@ struct BDesc {
     long long offnc;         // ... in the next level's batch vectors
     long long off_tmp;       // first row of the instance in the special-row scratch
     long long off_free;      // first entry in the coarsest-level free-DoF vectors
-    const int* list[SL_COUNT];
-    const T* cf[SL_COUNT];
+    const int* list[SL_COUNT];   // special rows: nodes
+    const int* cfg[SL_COUNT];    // ... and their configurations
     int cnt[SL_COUNT];
+    const T* cft;                // configuration table of this level of the instance
     const int* free_idx;     // coarsest level: SoA index of each free DoF
     const double* kinv;      // coarsest level: dense inverse, row-major nfree x nfree
     int nfree;
@@ -103,6 +104,7 @@ __device__ __forceinline__ bool tile_owner(const int* sp, const BatchArgs& a, in
 template <typename T, int FORM>
 __global__ void kb_vel_uniform(const BDesc<T>* __restrict__ D, BatchArgs a, int colour,
                                T* __restrict__ x, const T* __restrict__ f, T* __restrict__ out) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
     int i, j, k;
@@ -118,6 +120,7 @@ __global__ void kb_vel_uniform(const BDesc<T>* __restrict__ D, BatchArgs a, int 
 template <typename T, int FORM>
 __global__ void kb_vel_pass(const BDesc<T>* __restrict__ D, BatchArgs a, int colour, int sl,
                             T* __restrict__ x, const T* __restrict__ f, const T* __restrict__ tmp) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
     const long long slots = colour_slots(V.n1);
@@ -135,6 +138,7 @@ __global__ void kb_vel_pass(const BDesc<T>* __restrict__ D, BatchArgs a, int col
 template <typename T>
 __global__ void kb_vel_finish(const BDesc<T>* __restrict__ D, BatchArgs a, int colour, int sl,
                               const T* __restrict__ src, T* __restrict__ x, const T* __restrict__ tmp) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
     const long long slots = colour_slots(V.n1);
@@ -152,13 +156,14 @@ __global__ void kb_vel_finish(const BDesc<T>* __restrict__ D, BatchArgs a, int c
 template <typename T>
 __global__ void kb_pre_pass(const BDesc<T>* __restrict__ D, BatchArgs a, int colour, int sl,
                             T* __restrict__ x, const T* __restrict__ b) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
     const int cnt = d.cnt[sl];
     T* xv = x + 4 * d.offn;
     const T* g = b + 4 * d.offn + 3 * V.nn;
     int i, j, k;
-    if (item < 4LL * cnt) spec_row_quad<T, 2>(V, d.list[sl], cnt, d.cf[sl], xv, nullptr, g, item);
+    if (item < 4LL * cnt) spec_row_quad<T, 2>(V, d.list[sl], d.cfg[sl], d.cft, xv, nullptr, g, item);
     else if (item - 4LL * cnt < colour_slots(V.n1) && colour_slot(V.n1, colour, item - 4LL * cnt, i, j, k))
         pre_uniform_node<T>(V, i, j, k, xv, g);
     BATCH_END
@@ -168,6 +173,7 @@ template <typename T, int FORM>
 __global__ void kb_apply_uniform(const BDesc<T>* __restrict__ D, BatchArgs a,
                                  const T* __restrict__ x, T* __restrict__ y,
                                  const T* __restrict__ b) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> V = d.V;
     if (item >= V.nn) continue;
@@ -181,17 +187,18 @@ __global__ void kb_apply_uniform(const BDesc<T>* __restrict__ D, BatchArgs a,
 template <typename T, int MODE>
 __global__ void kb_spec(const BDesc<T>* __restrict__ D, BatchArgs a, int sl, T* __restrict__ x,
                         T* __restrict__ y, const T* __restrict__ b) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const int cnt = d.cnt[sl];
     if (item >= 4LL * cnt) continue;  // whole quads: tiles hold whole quads
     const LevelView<T> V = d.V;
     T* xv = x + 4 * d.offn;
     if (MODE == 1)
-        spec_row_quad<T, 1>(V, d.list[sl], cnt, d.cf[sl], xv, y + 3 * d.off_tmp, b + 4 * d.offn, item);
+        spec_row_quad<T, 1>(V, d.list[sl], d.cfg[sl], d.cft, xv, y + 3 * d.off_tmp, b + 4 * d.offn, item);
     else if (MODE == 2)
-        spec_row_quad<T, 2>(V, d.list[sl], cnt, d.cf[sl], xv, nullptr, b + 4 * d.offn + 3 * V.nn, item);
+        spec_row_quad<T, 2>(V, d.list[sl], d.cfg[sl], d.cft, xv, nullptr, b + 4 * d.offn + 3 * V.nn, item);
     else
-        spec_row_quad<T, MODE>(V, d.list[sl], cnt, d.cf[sl], xv, y + 4 * d.offn, b ? b + 4 * d.offn : nullptr,
+        spec_row_quad<T, MODE>(V, d.list[sl], d.cfg[sl], d.cft, xv, y + 4 * d.offn, b ? b + 4 * d.offn : nullptr,
                                item);
     BATCH_END
 }
@@ -199,6 +206,7 @@ __global__ void kb_spec(const BDesc<T>* __restrict__ D, BatchArgs a, int sl, T* 
 template <typename T>
 __global__ void kb_restrict(const BDesc<T>* __restrict__ D, BatchArgs a, const T* __restrict__ rf,
                             T* __restrict__ bc) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> C = d.C;
     if (item >= C.nn) continue;
@@ -210,6 +218,7 @@ __global__ void kb_restrict(const BDesc<T>* __restrict__ D, BatchArgs a, const T
 template <typename T>
 __global__ void kb_prolong(const BDesc<T>* __restrict__ D, BatchArgs a, const T* __restrict__ ec,
                            T* __restrict__ xf) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const LevelView<T> F = d.V;
     if (item >= F.nn) continue;
@@ -221,6 +230,7 @@ __global__ void kb_prolong(const BDesc<T>* __restrict__ D, BatchArgs a, const T*
 // Zero 4 x nodes of this level (next = 0) or of the next level (next = 1).
 template <typename T>
 __global__ void kb_zero(const BDesc<T>* __restrict__ D, BatchArgs a, int next, T* __restrict__ x) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     const long long len = 4 * (next ? d.C.nn : d.V.nn);
     if (item >= len) continue;
@@ -233,6 +243,7 @@ __global__ void kb_zero(const BDesc<T>* __restrict__ D, BatchArgs a, int next, T
 template <typename T>
 __global__ void kb_cgather(const BDesc<T>* __restrict__ D, BatchArgs a, const T* __restrict__ b,
                            double* __restrict__ bc) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     if (item >= d.nfree) continue;
     bc[d.off_free + item] = (double)b[4 * d.offn + d.free_idx[item]];
@@ -242,6 +253,7 @@ __global__ void kb_cgather(const BDesc<T>* __restrict__ D, BatchArgs a, const T*
 template <typename T>
 __global__ void kb_cmv(const BDesc<T>* __restrict__ D, BatchArgs a, const double* __restrict__ bc,
                        double* __restrict__ xc) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     // items per instance are 32 x nfree and tiles are whole warps: the test is warp-uniform
     const long long row = item >> 5;
@@ -260,6 +272,7 @@ __global__ void kb_cmv(const BDesc<T>* __restrict__ D, BatchArgs a, const double
 template <typename T>
 __global__ void kb_cscatter(const BDesc<T>* __restrict__ D, BatchArgs a, const double* __restrict__ xc,
                             T* __restrict__ x) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     if (item >= d.nfree) continue;
     x[4 * d.offn + d.free_idx[item]] = (T)xc[d.off_free + item];
@@ -272,6 +285,7 @@ __global__ void kb_cscatter(const BDesc<T>* __restrict__ D, BatchArgs a, const d
 __global__ void kb_vec(const BDesc<double>* __restrict__ D, BatchArgs a, int op,
                        double* __restrict__ y, const double* __restrict__ x,
                        const double* __restrict__ s) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     if (item >= 4 * d.V.nn) continue;
     const long long t = 4 * d.offn + item;
@@ -286,6 +300,7 @@ __global__ void kb_vec(const BDesc<double>* __restrict__ D, BatchArgs a, int op,
 // y32 = float(x / s[i]) (s == nullptr: no scaling)
 __global__ void kb_d2f(const BDesc<double>* __restrict__ D, BatchArgs a, float* __restrict__ y,
                        const double* __restrict__ x, const double* __restrict__ s) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     if (item >= 4 * d.V.nn) continue;
     const long long t = 4 * d.offn + item;
@@ -297,6 +312,7 @@ __global__ void kb_d2f(const BDesc<double>* __restrict__ D, BatchArgs a, float* 
 __global__ void kb_f2d(const BDesc<double>* __restrict__ D, BatchArgs a, int add,
                        double* __restrict__ y, const float* __restrict__ x,
                        const double* __restrict__ s) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     if (item >= 4 * d.V.nn) continue;
     const long long t = 4 * d.offn + item;
@@ -310,6 +326,7 @@ __global__ void kb_f2d(const BDesc<double>* __restrict__ D, BatchArgs a, int add
 __global__ void kb_maxpy(const BDesc<double>* __restrict__ D, BatchArgs a, double* __restrict__ w,
                          const double* __restrict__ V, long long stride, int nk,
                          const double* __restrict__ coef, int ldc, double sign) {
+    pdl_prologue();
     BATCH_TILES(D, a)
     if (item >= 4 * d.V.nn) continue;
     const long long t = 4 * d.offn + item;
@@ -336,6 +353,7 @@ __global__ void __launch_bounds__(DOT_TPB) kb_mdot(const BDesc<double>* __restri
                                                    const double* __restrict__ w,
                                                    const double* __restrict__ V, long long stride,
                                                    int nk, double* __restrict__ part) {
+    pdl_prologue();
     __shared__ int sp[MAX_BATCH + 1];
     __shared__ double red[DOT_TPB / 32];
     load_prefix(sp, a);
@@ -367,6 +385,7 @@ __global__ void __launch_bounds__(DOT_TPB) kb_mdot(const BDesc<double>* __restri
 // out[i * nk + k] = sum of the instance's tile partials, in tile order; optional sqrt.
 __global__ void kb_mdot_final(BatchArgs a, int nk, const double* __restrict__ part,
                               double* __restrict__ out, int take_sqrt) {
+    pdl_prologue();
     const int inst = blockIdx.x;
     if (inst >= a.count || (a.active && !a.active[inst])) return;
     const int t0 = a.prefix[inst], t1 = a.prefix[inst + 1];
@@ -488,20 +507,19 @@ static void set_work(Batch& B, Work& w, int tpb, int grid_cap, long long items_p
 }
 
 template <typename T>
-static void fill_lists(const Level& L, BDesc<T>& d);
-template <>
-void fill_lists<double>(const Level& L, BDesc<double>& d) {
-    const int* lists[SL_COUNT] = {L.spec_vel[0], L.spec_vel[1], L.spec_pre[0], L.spec_pre[1], L.spec_full, L.spec_prow};
-    const double* cfs[SL_COUNT] = {L.cf_vel_d[0], L.cf_vel_d[1], L.cf_pre_d[0], L.cf_pre_d[1], L.cf_full_d, L.cf_prow_d};
-    const int cnts[SL_COUNT] = {L.n_spec_vel[0], L.n_spec_vel[1], L.n_spec_pre[0], L.n_spec_pre[1], L.n_spec_full, L.n_spec_prow};
-    for (int q = 0; q < SL_COUNT; ++q) { d.list[q] = lists[q]; d.cf[q] = cfs[q]; d.cnt[q] = cnts[q]; }
-}
-template <>
-void fill_lists<float>(const Level& L, BDesc<float>& d) {
-    const int* lists[SL_COUNT] = {L.spec_vel[0], L.spec_vel[1], L.spec_pre[0], L.spec_pre[1], L.spec_full, L.spec_prow};
-    const float* cfs[SL_COUNT] = {L.cf_vel_f[0], L.cf_vel_f[1], L.cf_pre_f[0], L.cf_pre_f[1], L.cf_full_f, L.cf_prow_f};
-    const int cnts[SL_COUNT] = {L.n_spec_vel[0], L.n_spec_vel[1], L.n_spec_pre[0], L.n_spec_pre[1], L.n_spec_full, L.n_spec_prow};
-    for (int q = 0; q < SL_COUNT; ++q) { d.list[q] = lists[q]; d.cf[q] = cfs[q]; d.cnt[q] = cnts[q]; }
+static const T* level_cft(const Level& L);
+template <> const double* level_cft<double>(const Level& L) { return L.cft_d; }
+template <> const float* level_cft<float>(const Level& L) { return L.cft_f; }
+
+template <typename T>
+static void fill_lists(const Level& L, BDesc<T>& d) {
+    const SpecRows* rows[SL_COUNT] = {&L.vel[0], &L.vel[1], &L.pre[0], &L.pre[1], &L.full, &L.prow};
+    for (int q = 0; q < SL_COUNT; ++q) {
+        d.list[q] = rows[q]->node;
+        d.cfg[q] = rows[q]->cfg;
+        d.cnt[q] = rows[q]->n;
+    }
+    d.cft = level_cft<T>(L);
 }
 
 template <typename T>
@@ -563,7 +581,7 @@ template <typename... KArgs, typename... Args>
 static void blaunch(const Work& w, cudaStream_t s, void (*kernel)(KArgs...), Args... a) {
     if (!w.total) return;
     count_launches(1);
-    kernel<<<w.grid, w.tpb, 0, s>>>(a...);
+    launch_k(kernel, dim3(w.grid), dim3(w.tpb), s, a...);
 }
 
 // ---------------------------------------------------------------- batched cycle phases
@@ -714,7 +732,7 @@ static void bmdot(Batch& B, const double* w, const double* V, long long stride, 
     }
     blaunch(wd, s, kb_mdot, L.d64, args(B, wd, active), w, V, stride, nk, B.part);
     count_launches(1);
-    kb_mdot_final<<<B.count, 32, 0, s>>>(args(B, wd, active), nk, B.part, out, take_sqrt ? 1 : 0);
+    launch_k(kb_mdot_final, dim3(B.count), dim3(32), s, args(B, wd, active), nk, B.part, out, take_sqrt ? 1 : 0);
 }
 
 static void set_flags(Batch& B, int* dev, const std::vector<int>& f, cudaStream_t s) {
@@ -756,8 +774,10 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
     }
     for (int i = 1; i < count; ++i)
         if (descs[i].form != descs[0].form || descs[i].coarse_form != descs[0].coarse_form ||
-            descs[i].prec != descs[0].prec) {
-            set_error("every instance of a batch must use the same form, coarse_form and prec");
+            descs[i].prec != descs[0].prec || descs[i].coarsest_form != descs[0].coarsest_form ||
+            descs[i].coarse_correction != descs[0].coarse_correction) {
+            set_error("every instance of a batch must use the same form, coarse_form, coarsest_form, "
+                      "coarse_correction and prec");
             throw Fail{SDX_EINVAL};
         }
     Batch* B = new (std::nothrow) Batch();
@@ -789,7 +809,7 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
                 L.offn[i] = nodes;
                 nodes += Li.nn;
                 off_tmp[i] = rows;
-                rows += std::max(Li.n_spec_vel[0], Li.n_spec_vel[1]);
+                rows += std::max(Li.vel[0].n, Li.vel[1].n);
                 const bool coarsest = l == B->depth[i] - 1;
                 if (coarsest) {
                     off_free[i] = nfree;
@@ -804,25 +824,25 @@ static Batch* batch_create(const sdx_desc* descs, int count, int autotune) {
                     L.w[WK_CNODES].items[i] = Lc.nn;
                     if (l + 1 < B->depth[i] - 1) L.w[WK_ZEROC].items[i] = 4 * Lc.nn;
                     // special rows run one quad of lanes per row (the scatter uses the first quarter)
-                    L.w[WK_VEL0].items[i] = 4LL * Li.n_spec_vel[0];
-                    L.w[WK_VEL1].items[i] = 4LL * Li.n_spec_vel[1];
-                    L.w[WK_PRE0].items[i] = 4LL * Li.n_spec_pre[0];
-                    L.w[WK_PRE1].items[i] = 4LL * Li.n_spec_pre[1];
+                    L.w[WK_VEL0].items[i] = 4LL * Li.vel[0].n;
+                    L.w[WK_VEL1].items[i] = 4LL * Li.vel[1].n;
+                    L.w[WK_PRE0].items[i] = 4LL * Li.pre[0].n;
+                    L.w[WK_PRE1].items[i] = 4LL * Li.pre[1].n;
                     for (int c = 0; c < 2; ++c) {
-                        L.w[WK_VPASS0 + c].items[i] = colour_slots(Li.n + 1) + Li.n_spec_vel[c];
-                        L.w[WK_PPASS0 + c].items[i] = colour_slots(Li.n + 1) + 4LL * Li.n_spec_pre[c];
+                        L.w[WK_VPASS0 + c].items[i] = colour_slots(Li.n + 1) + Li.vel[c].n;
+                        L.w[WK_PPASS0 + c].items[i] = colour_slots(Li.n + 1) + 4LL * Li.pre[c].n;
                     }
                 }
                 // the finest level also serves the outer iteration (residuals of every instance)
                 if (l == 0) {
                     L.w[WK_NODES].items[i] = Li.nn;
-                    L.w[WK_FULL].items[i] = 4LL * Li.n_spec_full;
-                    L.w[WK_PROW].items[i] = 4LL * Li.n_spec_prow;
+                    L.w[WK_FULL].items[i] = 4LL * Li.full.n;
+                    L.w[WK_PROW].items[i] = 4LL * Li.prow.n;
                     L.w[WK_V4].items[i] = 4 * Li.nn;
                     L.w[WK_DOT].items[i] = 4 * Li.nn;
                 } else if (!coarsest) {
-                    L.w[WK_FULL].items[i] = 4LL * Li.n_spec_full;
-                    L.w[WK_PROW].items[i] = 4LL * Li.n_spec_prow;
+                    L.w[WK_FULL].items[i] = 4LL * Li.full.n;
+                    L.w[WK_PROW].items[i] = 4LL * Li.prow.n;
                 }
             }
             // the coarse correction of level l is zero-started on level l + 1's vectors

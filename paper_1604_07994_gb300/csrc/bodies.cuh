@@ -52,87 +52,217 @@ __host__ __device__ __forceinline__ long long colour_slots(int n1) {
     return (long long)((n1 + 1) / 2) * n1 * n1;
 }
 
+// ------------------------------------------------------------------ neighbourhood loads
+// The uniform-node bodies load a node's whole neighbourhood first and test whether the node is
+// special only afterwards, so that the test (which waits for the info word) does not hold back
+// the other loads: one round trip to memory per node instead of two.  The loads are volatile so
+// that they are issued where they stand.  With NC they use the read-only path, valid when no
+// thread of the launch writes what another reads (one colour pass or apply per launch: the
+// colouring, x != y); the fused smoothing kernels, whose phases read what earlier phases of the
+// same launch wrote, use plain loads (NC = false), which their barriers' acquire makes see
+// those writes.
+template <bool NC>
+__device__ __forceinline__ float ldx(const float* p) {
+    float v;
+    if (NC) asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+template <bool NC>
+__device__ __forceinline__ double ldx(const double* p) {
+    double v;
+    if (NC) asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    else asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    return v;
+}
+template <typename T>
+__device__ __forceinline__ T ldro(const T* p) { return ldx<true>(p); }
+__device__ __forceinline__ unsigned ldro_u16(const uint16_t* p) {
+    unsigned v;
+    asm volatile("ld.global.nc.u16 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+__device__ __forceinline__ unsigned ldro_u8(const uint8_t* p) {
+    unsigned v;
+    asm volatile("ld.global.nc.u8 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
+// Node offsets of the seven Kuhn directions ex, ey, ez, exy, exz, eyz, exyz.
+template <typename T>
+__device__ __forceinline__ void kuhn_offsets(const LevelView<T>& L, long long off[7]) {
+    off[EX] = 1; off[EY] = L.s1; off[EZ] = L.s2; off[EXY] = 1 + L.s1; off[EXZ] = 1 + L.s2;
+    off[EYZ] = L.s1 + L.s2; off[EXYZ] = 1 + L.s1 + L.s2;
+}
+
+// The 14 neighbours v(b - d), v(b + d) of node b (no centre).
+template <bool NC, typename T>
+__device__ __forceinline__ void ld_nb14(const T* v, long long b, const long long off[7], T m[7], T p[7]) {
+#pragma unroll
+    for (int d = 0; d < 7; ++d) {
+        m[d] = ldx<NC>(v + b - off[d]);
+        p[d] = ldx<NC>(v + b + off[d]);
+    }
+}
+
+__device__ __forceinline__ bool interior_node(int n, int i, int j, int k) {
+    return i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
+}
+
+// Sum over the seven Kuhn directions d of sum_i s_i(d) A_d(u_i), where s_i(d) = +1 if d has a
+// component along axis i and -1 otherwise: with it, B u = h^2 [T / 12 + (A_ex(u_x) + A_ey(u_y) +
+// A_ez(u_z)) / 6] (the B stencil of stencil.cuh, its e_i weight 1/4 split as 1/12 + 1/6).
+template <typename T>
+__device__ __forceinline__ void bu_sums(const T um[3][7], const T up[3][7], T& tsum, T& diag) {
+    T A[3][7];
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 7; ++d) A[c][d] = um[c][d] - up[c][d];
+    tsum = ((A[0][EX] - A[1][EX] - A[2][EX]) + (A[1][EY] - A[0][EY] - A[2][EY])) +
+           ((A[2][EZ] - A[0][EZ] - A[1][EZ]) + (A[0][EXY] + A[1][EXY] - A[2][EXY])) +
+           ((A[0][EXZ] + A[2][EXZ] - A[1][EXZ]) + (A[1][EYZ] + A[2][EYZ] - A[0][EYZ])) +
+           (A[0][EXYZ] + A[1][EXYZ] + A[2][EXYZ]);
+    diag = A[0][EX] + A[1][EY] + A[2][EZ];
+}
+
+// The seven pressure differences A_d(p) and their combination D = sum of the four diagonal
+// directions minus the three axes (B^T p of stencil.cuh: row j is
+// -h^2 [A_j / 3 - A_pair(j) / 6 + D / 12]).
+template <typename T>
+__device__ __forceinline__ T bt_diffs(const T pm[7], const T pp[7], T A[7]) {
+#pragma unroll
+    for (int d = 0; d < 7; ++d) A[d] = pm[d] - pp[d];
+    return (A[EXY] + A[EXZ] + A[EYZ] + A[EXYZ]) - (A[EX] + A[EY] + A[EZ]);
+}
+
 // ------------------------------------------------------------------ apply / residual
-// y = K x (b == nullptr) or y = b - K x at one non-special node.
+// y = K x (b == nullptr) or y = b - K x at one non-special node (a_tr / gradient form: the
+// velocity block is the mu-weighted 7-point Laplacian; strain form: stencil.cuh's a_sym rows).
 template <typename T, int FORM>
 __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long long node,
                                                    const T* __restrict__ x, T* __restrict__ y,
                                                    const T* __restrict__ b) {
-    if (L.info[node] & INFO_SPECIAL) return;
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
-    const int id = uniform_id(L, i, j, k);
-    const T muh = L.muh[id];
-    const T tauh = L.tauh[id];
-    const T h2 = L.h * L.h;
+    if (!interior_node(L.n, i, j, k)) return;  // boundary nodes are special rows
     const long long nn = L.nn;
-    Nb15<T> P;
-    load_nb15(x + 3 * nn, node, L, P);
-    T hbt[3];
-    bt3(P, h2, hbt);
-    T bu = 0;
-    Nb15<T> U[3];
+    long long off[7];
+    kuhn_offsets(L, off);
+    const unsigned inf = ldro_u16(L.info + node);
+    const int id = (int)ldro_u8(L.cid + i + (long long)L.P * (j + (long long)L.P * k));
+    T pm[7], pp[7], um[3][7], up[3][7], uc[3];
+    const T pc = ldro(x + 3 * nn + node);
+    ld_nb14<true>(x + 3 * nn, node, off, pm, pp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        load_nb15(x + c * nn, node, L, U[c]);
-        bu += bstencil(U[c], c);
+        uc[c] = ldro(x + c * nn + node);
+        ld_nb14<true>(x + c * nn, node, off, um[c], up[c]);
     }
+    T bv[4] = {0, 0, 0, 0};
+    if (b)
 #pragma unroll
-    for (int jj = 0; jj < 3; ++jj) {
-        T lap = T(6) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ));
-        if (FORM == FORM_SYM) {
-            lap += T(2) * U[jj].c - U[jj].S(jj);
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-                if (ii != jj) lap += xstencil(U[ii], ii, jj);
-        }
-        const T row = muh * lap - hbt[jj];
-        y[jj * nn + node] = b ? b[jj * nn + node] - row : row;
-    }
-    const T cp = tauh * (T(6) * P.c - (P.S(EX) + P.S(EY) + P.S(EZ)));
-    const T rowp = h2 * bu - cp;
-    y[3 * nn + node] = b ? b[3 * nn + node] - rowp : rowp;
-}
-
-// ------------------------------------------------------------------ smoother passes
-// Velocity update of one non-special node (i, j, k): u_j += (f_j - (A u + B^T p)_j) / diag.
-// In place for a_tr / gradient form (rows read only other-colour velocities); the strain
-// form writes into `out` (3 components) because its cross-couplings read same-colour nodes.
-template <typename T, int FORM>
-__device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, int j, int k,
-                                                 T* __restrict__ x, const T* __restrict__ f,
-                                                 T* __restrict__ out) {
-    const long long node = i + L.s1 * j + L.s2 * k;
-    if (L.info[node] & INFO_SPECIAL) return;
-    const int id = uniform_id(L, i, j, k);
+        for (int c = 0; c < 4; ++c) bv[c] = ldro(b + c * nn + node);
+    if (inf & INFO_SPECIAL) return;
     const T muh = L.muh[id];
-    const T inv = L.idA[id];
-    const T h2 = L.h * L.h;
-    const long long nn = L.nn;
-    Nb15<T> P;
-    load_nb15(x + 3 * nn, node, L, P);
-    T hbt[3];
-    bt3(P, h2, hbt);
+    const T tauh = L.tauh[id];
+    T A[7];
+    const T D = bt_diffs(pm, pp, A);
+    const T btD = -L.h2_12 * D;
+    const int pair[3] = {EYZ, EXZ, EXY};
+    T row[3];
     if (FORM == FORM_SYM) {
         Nb15<T> U[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) load_nb15(x + c * nn, node, L, U[c]);
+        for (int c = 0; c < 3; ++c) {
+            U[c].c = uc[c];
+#pragma unroll
+            for (int d = 0; d < 7; ++d) { U[c].m[d] = um[c][d]; U[c].p[d] = up[c][d]; }
+        }
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             T lap = T(8) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj);
 #pragma unroll
             for (int ii = 0; ii < 3; ++ii)
                 if (ii != jj) lap += xstencil(U[ii], ii, jj);
-            const T row = muh * lap - hbt[jj];
-            out[jj * nn + node] = U[jj].c + (f[jj * nn + node] - row) * inv;
+            row[jj] = fma(muh, lap, fma(-L.h2_3, A[jj], fma(L.h2_6, A[pair[jj]], btD)));
         }
     } else {
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
-            T* u = x + jj * nn;
-            const T c = u[node];
-            const T row = muh * lap7(u, node, L, c) - hbt[jj];
-            u[node] = c + (f[jj * nn + node] - row) * inv;
+            const T s = ((um[jj][EX] + up[jj][EX]) + (um[jj][EY] + up[jj][EY])) + (um[jj][EZ] + up[jj][EZ]);
+            row[jj] = fma(muh, fma(T(6), uc[jj], -s), fma(-L.h2_3, A[jj], fma(L.h2_6, A[pair[jj]], btD)));
+        }
+    }
+    T tsum, dsum;
+    bu_sums(um, up, tsum, dsum);
+    const T sp = ((pm[EX] + pp[EX]) + (pm[EY] + pp[EY])) + (pm[EZ] + pp[EZ]);
+    const T rowp = fma(L.h2_12, tsum, fma(L.h2_6, dsum, -tauh * fma(T(6), pc, -sp)));
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) y[jj * nn + node] = b ? bv[jj] - row[jj] : row[jj];
+    y[3 * nn + node] = b ? bv[3] - rowp : rowp;
+}
+
+// ------------------------------------------------------------------ smoother passes
+// Velocity update of one non-special node (i, j, k): u_j += (f_j - (A u + B^T p)_j) / diag.
+// For a_tr and the gradient form the uniform row is mu h (6 u_j - S_j) + (B^T p)_j with S_j the
+// sum of the six axis neighbours and diag = 6 mu h, so the update does not depend on the old
+// u_j: u_j = S_j / 6 + (f_j - (B^T p)_j) / (6 mu h); these rows read only velocities of the other
+// colour, in place.  The strain form (diag 8 mu h) reads same-colour velocities through its
+// cross-couplings and writes the new values into `out` (3 components).
+template <typename T, int FORM, bool NC = true>
+__device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, int j, int k,
+                                                 T* __restrict__ x, const T* __restrict__ f,
+                                                 T* __restrict__ out) {
+    if (!interior_node(L.n, i, j, k)) return;
+    const long long node = i + L.s1 * j + L.s2 * k;
+    const long long nn = L.nn;
+    long long off[7];
+    kuhn_offsets(L, off);
+    const unsigned inf = ldro_u16(L.info + node);
+    const int id = (int)ldro_u8(L.cid + i + (long long)L.P * (j + (long long)L.P * k));
+    T pm[7], pp[7], fv[3];
+    ld_nb14<NC>(x + 3 * nn, node, off, pm, pp);
+    const int pair[3] = {EYZ, EXZ, EXY};
+    if (FORM == FORM_SYM) {
+        Nb15<T> U[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            U[c].c = ldx<NC>(x + c * nn + node);
+            ld_nb14<NC>(x + c * nn, node, off, U[c].m, U[c].p);
+            fv[c] = ldx<NC>(f + c * nn + node);
+        }
+        if (inf & INFO_SPECIAL) return;
+        const T idA = L.idA[id], a1 = L.a1[id], a2 = L.a2[id], a3 = L.a3[id];
+        T A[7];
+        const T aD = a3 * bt_diffs(pm, pp, A);
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            // u_j = (S_xyz(u_j) + S_j(u_j) - sum_i X_ij(u_i)) / 8 + (f_j - (B^T p)_j) / (8 mu h)
+            T w = (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) + U[jj].S(jj);
+#pragma unroll
+            for (int ii = 0; ii < 3; ++ii)
+                if (ii != jj) w -= xstencil(U[ii], ii, jj);
+            out[jj * nn + node] = fma(w, T(0.125), fma(idA, fv[jj], fma(a1, A[jj], fma(a2, A[pair[jj]], aD))));
+        }
+    } else {
+        T um[3][3], up[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const T* u = x + c * nn + node;
+            um[c][0] = ldx<NC>(u - 1);    up[c][0] = ldx<NC>(u + 1);
+            um[c][1] = ldx<NC>(u - L.s1); up[c][1] = ldx<NC>(u + L.s1);
+            um[c][2] = ldx<NC>(u - L.s2); up[c][2] = ldx<NC>(u + L.s2);
+            fv[c] = ldx<NC>(f + c * nn + node);
+        }
+        if (inf & INFO_SPECIAL) return;
+        const T idA = L.idA[id], a1 = L.a1[id], a2 = L.a2[id], a3 = L.a3[id];
+        T A[7];
+        const T aD = a3 * bt_diffs(pm, pp, A);
+#pragma unroll
+        for (int jj = 0; jj < 3; ++jj) {
+            const T s = ((um[jj][0] + up[jj][0]) + (um[jj][1] + up[jj][1])) + (um[jj][2] + up[jj][2]);
+            x[jj * nn + node] = fma(s, T(1.0 / 6.0), fma(idA, fv[jj], fma(a1, A[jj], fma(a2, A[pair[jj]], aD))));
         }
     }
 }
@@ -147,52 +277,60 @@ __device__ __forceinline__ void vel_copy_node(const LevelView<T>& L, int i, int 
     for (int c = 0; c < 3; ++c) x[c * L.nn + node] = src[c * L.nn + node];
 }
 
-// Pressure Gauss-Seidel on C p = B u - g with relaxation OMEGA at one non-special node.
-template <typename T>
+// Pressure Gauss-Seidel on C p = B u - g with relaxation OMEGA at one non-special node:
+// p += omega (B u - tau h (6 p - S_p) - g) / (6 tau h), evaluated as
+// (1 - omega) p + (omega / 6) S_p + idC h^2 B u - idC g with idC = omega / (6 tau h).
+template <typename T, bool NC = true>
 __device__ __forceinline__ void pre_uniform_node(const LevelView<T>& L, int i, int j, int k,
                                                  T* __restrict__ x, const T* __restrict__ g) {
+    if (!interior_node(L.n, i, j, k)) return;
     const long long node = i + L.s1 * j + L.s2 * k;
-    if (L.info[node] & INFO_SPECIAL) return;
-    const int id = uniform_id(L, i, j, k);
-    const T h2 = L.h * L.h;
     const long long nn = L.nn;
-    T bu = 0;
+    long long off[7];
+    kuhn_offsets(L, off);
+    const unsigned inf = ldro_u16(L.info + node);
+    const int id = (int)ldro_u8(L.cid + i + (long long)L.P * (j + (long long)L.P * k));
+    T um[3][7], up[3][7];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        Nb15<T> U;
-        load_nb15(x + c * nn, node, L, U);
-        bu += bstencil(U, c);
-    }
+    for (int c = 0; c < 3; ++c) ld_nb14<NC>(x + c * nn, node, off, um[c], up[c]);
     T* p = x + 3 * nn;
-    const T pc = p[node];
-    const T cp = L.tauh[id] * lap7(p, node, L, pc);
-    const T s = h2 * bu - cp - g[node];
-    p[node] = pc + s * L.idC[id];
+    const T pc = ldx<NC>(p + node);
+    const T sp = ((ldx<NC>(p + node - 1) + ldx<NC>(p + node + 1)) + (ldx<NC>(p + node - L.s1) + ldx<NC>(p + node + L.s1))) +
+                 (ldx<NC>(p + node - L.s2) + ldx<NC>(p + node + L.s2));
+    const T gv = ldx<NC>(g + node);
+    if (inf & INFO_SPECIAL) return;
+    T tsum, dsum;
+    bu_sums(um, up, tsum, dsum);
+    const T idC = L.idC[id], k12 = L.k12[id];
+    p[node] = fma(k12, fma(T(2), dsum, tsum), fma(-idC, gv, fma(T(OMEGA / 6.0), sp, T(1.0 - OMEGA) * pc)));
 }
 
 // ------------------------------------------------------------------ special rows
-// One special row from its stored coefficients (SoA [coefficient][count]; column
-// (component c, Kuhn offset d) is c * 15 + d, row component r adds r * 60), evaluated by a
-// quad of four consecutive lanes: lane q of the quad takes the columns of solution component
-// q over the 15 offsets, and the four partial sums are added with two quad shuffles.  Lane 0 of
-// the quad writes the result.  `quad` = the slot index times 4 plus q; every lane of a quad
-// must call this with the same slot (mask: the quad's lanes in the warp).
+// One special row from its configuration's coefficients (sdx_internal.h: column (component c,
+// Kuhn offset d) of row component r at r * 60 + c * 15 + d), evaluated by a quad of four
+// consecutive lanes: lane q of the quad takes the columns of solution component q over the 15
+// offsets, and the four partial sums are added with two quad shuffles.  Lane 0 of the quad
+// writes the result.  `quad` = the slot index times 4 plus q; every lane of a quad must call
+// this with the same slot (mask: the quad's lanes in the warp).
 // MODE 0: y = K x (or b - K x) on a full row; MODE 3: the same on a pressure-only row
 // (velocity rows written as 0); MODE 1: new velocity values of a colour into
 // y[3 * slot + r]; MODE 2: pressure Gauss-Seidel in place (b = g).
 template <typename T, int MODE>
 __device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* __restrict__ list,
-                                              int count, const T* __restrict__ cf,
-                                              T* __restrict__ x, T* __restrict__ y,
-                                              const T* __restrict__ b, long long quad) {
+                                              const int* __restrict__ cfgs,
+                                              const T* __restrict__ cft, T* __restrict__ x,
+                                              T* __restrict__ y, const T* __restrict__ b,
+                                              long long quad) {
     const int slot = (int)(quad >> 2);
     const int q = (int)(quad & 3);
     const unsigned mask = 0xFu << (threadIdx.x & 28);
     const long long node = list[slot];
+    const T* __restrict__ cf = cft + (long long)cfgs[slot] * CFG_STRIDE;
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
     const long long nn = L.nn;
-    constexpr int NR = MODE == 0 ? 4 : (MODE == 1 ? 3 : 1);  // row components stored
+    constexpr int NR = MODE == 0 ? 4 : (MODE == 1 ? 3 : 1);  // row components evaluated
+    constexpr int R0 = (MODE == 0 || MODE == 1) ? 0 : 3;     // first row component
     T acc[NR];
 #pragma unroll
     for (int r = 0; r < NR; ++r) acc[r] = T(0);
@@ -203,7 +341,7 @@ __device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* 
         if (a < 0 || bb < 0 || cc < 0 || a >= L.n1 || bb >= L.n1 || cc >= L.n1) continue;
         const T xv = xq[a + L.s1 * bb + L.s2 * cc];
 #pragma unroll
-        for (int r = 0; r < NR; ++r) acc[r] += cf[(long long)(r * 60 + q * 15 + d) * count + slot] * xv;
+        for (int r = 0; r < NR; ++r) acc[r] += cf[(R0 + r) * 60 + q * 15 + d] * xv;
     }
 #pragma unroll
     for (int r = 0; r < NR; ++r) {
@@ -228,12 +366,12 @@ __device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* 
         for (int r = 0; r < 3; ++r) {
             T v = T(0);
             if (!(inf & (1u << r)))
-                v = x[r * nn + node] + (b[r * nn + node] - acc[r]) / cf[(long long)(180 + r) * count + slot];
+                v = x[r * nn + node] + (b[r * nn + node] - acc[r]) / cf[CFG_DIAG_A + r];
             y[3 * (long long)slot + r] = v;
         }
     } else {
         T* p = x + 3 * nn;
-        p[node] = p[node] + T(OMEGA) * (acc[0] - b[node]) / cf[(long long)60 * count + slot];
+        p[node] = p[node] + T(OMEGA) * (acc[0] - b[node]) / cf[CFG_DIAG_C];
     }
 }
 

@@ -25,6 +25,7 @@ inline unsigned blocks_for(long long count, int tpb = TPB) {
 template <typename T, int FORM>
 __global__ void k_apply_uniform(LevelView<T> L, const T* __restrict__ x, T* __restrict__ y,
                                 const T* __restrict__ b) {
+    pdl_prologue();
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= L.nn) return;
     apply_uniform_node<T, FORM>(L, node, x, y, b);
@@ -39,6 +40,7 @@ template <typename T, int FORM>
 __global__ void k_vel_uniform(LevelView<T> L, int colour, T* __restrict__ x,
                               const T* __restrict__ f, T* __restrict__ out,
                               const int* __restrict__ list, int cnt, const T* __restrict__ tmp) {
+    pdl_prologue();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long slots = colour_slots(L.n1);
     int i, j, k;
@@ -49,12 +51,29 @@ __global__ void k_vel_uniform(LevelView<T> L, int colour, T* __restrict__ x,
     }
 }
 
+// Strain form, first launch of a colour pass: the colour's special rows (one quad of lanes each,
+// first so that quads stay aligned) stage their new values in `tmp`, its uniform rows write theirs
+// into `out`; nothing writes x, so both groups read the values from before the pass.
+template <typename T>
+__global__ void k_vel_sym_stage(LevelView<T> L, int colour, const T* __restrict__ x,
+                                const T* __restrict__ f, T* __restrict__ out, const int* __restrict__ list,
+                                const int* __restrict__ cfgs, int cnt, const T* __restrict__ cft,
+                                T* __restrict__ tmp) {
+    pdl_prologue();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    int i, j, k;
+    if (t < 4LL * cnt) spec_row_quad<T, 1>(L, list, cfgs, cft, const_cast<T*>(x), tmp, f, t);
+    else if (colour_slot(L.n1, colour, t - 4LL * cnt, i, j, k))
+        vel_uniform_node<T, FORM_SYM>(L, i, j, k, const_cast<T*>(x), f, out);
+}
+
 // Strain form (whose uniform rows read same-colour velocities, so the new values were written
 // to `src`): copy the colour's uniform values back and scatter its staged special rows.
 template <typename T>
 __global__ void k_vel_copy_colour(LevelView<T> L, int colour, const T* __restrict__ src,
                                   T* __restrict__ x, const int* __restrict__ list, int cnt,
                                   const T* __restrict__ tmp) {
+    pdl_prologue();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     const long long slots = colour_slots(L.n1);
     int i, j, k;
@@ -71,27 +90,29 @@ __global__ void k_vel_copy_colour(LevelView<T> L, int colour, const T* __restric
 // the Kuhn mesh) and u, which this pass does not write.
 template <typename T>
 __global__ void k_pre_uniform(LevelView<T> L, int colour, T* __restrict__ x,
-                              const T* __restrict__ g, const int* __restrict__ list, int cnt,
-                              const T* __restrict__ cf) {
+                              const T* __restrict__ g, const int* __restrict__ list,
+                              const int* __restrict__ cfgs, int cnt, const T* __restrict__ cft) {
+    pdl_prologue();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     int i, j, k;
-    if (t < 4LL * cnt) spec_row_quad<T, 2>(L, list, cnt, cf, x, nullptr, g, t);
+    if (t < 4LL * cnt) spec_row_quad<T, 2>(L, list, cfgs, cft, x, nullptr, g, t);
     else if (colour_slot(L.n1, colour, t - 4LL * cnt, i, j, k)) pre_uniform_node<T>(L, i, j, k, x, g);
 }
 
 // ------------------------------------------------------------------ special rows as stencils
-// Coefficients of special rows by evaluating the element-wise row on unit vectors: thread
-// (slot, col) with col = c * 15 + d applies the row of node list[slot] to the unit vector at
-// (component c, node + offset d).  rows: first row component stored (0 velocity / 3 pressure),
-// nrow: number of row components stored; diag: append diag(A) rows or diag(C).
+// Coefficients of the special-row configurations by evaluating the element-wise row of a
+// representative node on unit vectors: thread (cfg, col) with col = c * 15 + d applies the row
+// of node rep[cfg] to the unit vector at (component c, node + offset d) and stores the four row
+// components; column 0 also stores diag(A) (three velocity rows) and diag(C).
 template <int FORM>
-__global__ void k_build_coef(LevelView<double> L, const int* __restrict__ list, int count, int r0,
-                             int nrow, bool diag, double* __restrict__ out) {
+__global__ void k_build_cfg(LevelView<double> L, const int* __restrict__ rep, int ncfg,
+                            double* __restrict__ out) {
+    pdl_prologue();
     const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 60LL * count) return;
-    const int slot = (int)(t / 60), col = (int)(t % 60);
+    if (t >= 60LL * ncfg) return;
+    const int cfg = (int)(t / 60), col = (int)(t % 60);
     const int c = col / 15, d = col % 15;
-    const long long node = list[slot];
+    const long long node = rep[cfg];
     int i, j, k;
     node_ijk(node, L.n1, i, j, k);
     const int a = i + KOFF15[d][0], bb = j + KOFF15[d][1], cc = k + KOFF15[d][2];
@@ -101,38 +122,36 @@ __global__ void k_build_coef(LevelView<double> L, const int* __restrict__ list, 
     genrow_zero(R);
     const UnitAcc<double> X{c, inside ? a + L.s1 * bb + L.s2 * cc : -1};
     for (int q = 0; q < 24; ++q) tet_row<double, FORM, false>(L, X, i, j, k, q, (inf & INFO_IFACE) != 0, R);
-    for (int r = 0; r < nrow; ++r) {
-        const int rc = r0 + r;
-        const double v = rc < 3 ? R.au[rc] + R.btp[rc] : R.bu - R.cp;
-        out[(long long)(r * 60 + col) * count + slot] = v;
-    }
-    if (diag && col == 0) {
-        if (r0 == 0)
-            for (int r = 0; r < 3; ++r) out[(long long)(180 + r) * count + slot] = R.dA[r];
-        else
-            out[(long long)60 * count + slot] = R.dC;
+    double* o = out + (long long)cfg * CFG_STRIDE;
+    for (int r = 0; r < 4; ++r) o[r * 60 + col] = r < 3 ? R.au[r] + R.btp[r] : R.bu - R.cp;
+    if (col == 0) {
+        for (int r = 0; r < 3; ++r) o[CFG_DIAG_A + r] = R.dA[r];
+        o[CFG_DIAG_C] = R.dC;
     }
 }
 
 __global__ void k_d2f_plain(float* y, const double* x, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] = (float)x[t];
 }
 
 // One quad of lanes per special row (4 * count threads).
 template <typename T, int MODE>
-__global__ void k_spec_rows(LevelView<T> L, const int* __restrict__ list, int count,
-                            const T* __restrict__ cf, T* __restrict__ x, T* __restrict__ y,
+__global__ void k_spec_rows(LevelView<T> L, const int* __restrict__ list, const int* __restrict__ cfgs,
+                            int count, const T* __restrict__ cft, T* __restrict__ x, T* __restrict__ y,
                             const T* __restrict__ b) {
+    pdl_prologue();
     const long long quad = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (quad >= 4LL * count) return;  // whole quads: 4 * count and blockDim are multiples of 4
-    spec_row_quad<T, MODE>(L, list, count, cf, x, y, b, quad);
+    spec_row_quad<T, MODE>(L, list, cfgs, cft, x, y, b, quad);
 }
 
 // ------------------------------------------------------------------ transfers
 template <typename T>
 __global__ void k_restrict(LevelView<T> F, LevelView<T> C, const T* __restrict__ rf,
                            T* __restrict__ bc) {
+    pdl_prologue();
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= C.nn) return;
     restrict_node<T>(F, C, rf, bc, node);
@@ -141,6 +160,7 @@ __global__ void k_restrict(LevelView<T> F, LevelView<T> C, const T* __restrict__
 template <typename T>
 __global__ void k_prolong_add(LevelView<T> F, LevelView<T> C, const T* __restrict__ ec,
                               T* __restrict__ xf) {
+    pdl_prologue();
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= F.nn) return;
     prolong_node<T>(F, C, ec, xf, node);
@@ -149,6 +169,7 @@ __global__ void k_prolong_add(LevelView<T> F, LevelView<T> C, const T* __restric
 // ------------------------------------------------------------------ right-hand side
 // Velocity rows: lumped mass times nodal forcing; pressure rows: -sum_T tau_T |T| fbar.grad lambda_b.
 __global__ void k_rhs(LevelView<double> L, const double* __restrict__ f, double* __restrict__ bvec) {
+    pdl_prologue();
     long long node = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (node >= L.nn) return;
     int bi, bj, bk;
@@ -200,38 +221,46 @@ __global__ void k_rhs(LevelView<double> L, const double* __restrict__ f, double*
 // ------------------------------------------------------------------ vectors
 template <typename T>
 __global__ void k_zero(T* v, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) v[t] = T(0);
 }
 __global__ void k_axpy_dev(double* y, const double* x, const double* alpha, double sign, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] += sign * (*alpha) * x[t];
 }
 __global__ void k_axpy(double* y, const double* x, double alpha, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] += alpha * x[t];
 }
 __global__ void k_scale_dev(double* y, const double* x, const double* s, bool recip, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] = recip ? x[t] / (*s) : x[t] * (*s);
 }
 __global__ void k_copy(double* y, const double* x, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] = x[t];
 }
 // y = float(x / s)
 __global__ void k_d2f(float* y, const double* x, const double* s, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] = (float)(s ? x[t] / (*s) : x[t]);
 }
 // y += double(x) * s
 __global__ void k_f2d_add(double* y, const float* x, const double* s, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] += (double)x[t] * (s ? *s : 1.0);
 }
 
 // y = double(x) * s
 __global__ void k_f2d(double* y, const float* x, const double* s, long long count) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t < count) y[t] = (double)x[t] * (s ? *s : 1.0);
 }
@@ -239,6 +268,7 @@ __global__ void k_f2d(double* y, const float* x, const double* s, long long coun
 constexpr int RED_TPB = 512;
 __global__ void k_dot_part(const double* __restrict__ x, const double* __restrict__ y, long long count,
                            double* __restrict__ part) {
+    pdl_prologue();
     __shared__ double sh[RED_TPB / 32];
     double acc = 0;
     for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < count;
@@ -254,6 +284,7 @@ __global__ void k_dot_part(const double* __restrict__ x, const double* __restric
     }
 }
 __global__ void k_dot_final(const double* __restrict__ part, int nparts, double* out) {
+    pdl_prologue();
     __shared__ double sh[32];
     double acc = 0;
     for (int t = threadIdx.x; t < nparts; t += blockDim.x) acc += part[t];
@@ -271,18 +302,21 @@ __global__ void k_dot_final(const double* __restrict__ part, int nparts, double*
 template <typename T>
 __global__ void k_gather_free(const int* __restrict__ idx, int nf, const T* __restrict__ v,
                               double* __restrict__ out) {
+    pdl_prologue();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < nf) out[t] = (double)v[idx[t]];
 }
 template <typename T>
 __global__ void k_scatter_free(const int* __restrict__ idx, int nf, const double* __restrict__ v,
                                T* __restrict__ out) {
+    pdl_prologue();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t < nf) out[idx[t]] = (T)v[t];
 }
 // y = M x, M dense row-major [n x n]; one warp per row
 __global__ void k_dense_mv(const double* __restrict__ M, int n, const double* __restrict__ x,
                            double* __restrict__ y) {
+    pdl_prologue();
     int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     int lane = threadIdx.x & 31;
     if (warp >= n) return;
@@ -295,6 +329,7 @@ __global__ void k_dense_mv(const double* __restrict__ M, int n, const double* __
 
 // Gauss-Jordan on the augmented [A | I] (n x 2n, row-major), partial pivoting.
 __global__ void k_gj_pivot(double* aug, int n, int k, int* status) {
+    pdl_prologue();
     // single block: find argmax |aug[i][k]|, i >= k; swap into row k; normalise row k
     __shared__ double sv[1024];
     __shared__ int si[1024];
@@ -331,10 +366,12 @@ __global__ void k_gj_pivot(double* aug, int n, int k, int* status) {
     }
 }
 __global__ void k_gj_col(const double* aug, int n, int k, double* col) {
+    pdl_prologue();
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) col[i] = aug[(long long)i * 2 * n + k];
 }
 __global__ void k_gj_elim(double* aug, int n, int k, const double* col) {
+    pdl_prologue();
     const int w = 2 * n;
     int c = blockIdx.x * blockDim.x + threadIdx.x;
     int i = blockIdx.y;
@@ -344,12 +381,14 @@ __global__ void k_gj_elim(double* aug, int n, int k, const double* col) {
     aug[(long long)i * w + c] -= f * aug[(long long)k * w + c];
 }
 __global__ void k_gj_extract(const double* aug, int n, double* inv) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * n) return;
     long long i = t / n, c = t % n;
     inv[t] = aug[i * 2 * n + n + c];
 }
 __global__ void k_gj_init(double* aug, const double* a, int n) {
+    pdl_prologue();
     long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (long long)n * 2 * n) return;
     long long i = t / (2 * n), c = t % (2 * n);
@@ -401,8 +440,9 @@ struct CoopArgs {
     T* x;
     const T* b;
     int steps;
-    const int* sv[2]; const T* cv[2]; int nv[2];   // special velocity rows per colour
-    const int* sp[2]; const T* cp[2]; int np[2];   // special pressure rows per colour
+    const int* sv[2]; const int* cv[2]; int nv[2];   // special velocity rows per colour (nodes, configurations)
+    const int* sp[2]; const int* cp[2]; int np[2];   // special pressure rows per colour
+    const T* cft;                                    // configuration table of the level
     T* tmp;       // staged special velocity values (3 per row)
     T* sym;       // strain form: new values of the uniform nodes (3 components)
     unsigned* bar;  // [2]: arrivals, generation
@@ -438,12 +478,12 @@ __device__ __forceinline__ void uzawa_coop_body(const CoopArgs<T>& a) {
             const int c = q & 1;  // colours 0, 1, 0
             const int nv = a.nv[c];
             for (long long t = tid; t < 4LL * nv; t += nth)  // quads of lanes (nth is a multiple of 4)
-                spec_row_quad<T, 1>(L, a.sv[c], nv, a.cv[c], x, a.tmp, b, t);
+                spec_row_quad<T, 1>(L, a.sv[c], a.cv[c], a.cft, x, a.tmp, b, t);
             if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
             if (FORM == FORM_SYM) {
                 for (long long t = tid; t < slots; t += nth) {
                     int i, j, k;
-                    if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, b, a.sym);
+                    if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM, false>(L, i, j, k, x, b, a.sym);
                 }
                 if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
                 for (long long t = tid; t < slots + nv; t += nth) {
@@ -455,7 +495,7 @@ __device__ __forceinline__ void uzawa_coop_body(const CoopArgs<T>& a) {
                 for (long long t = tid; t < slots + nv; t += nth) {
                     int i, j, k;
                     if (t >= slots) vel_scatter_slot<T>(a.sv[c], (int)(t - slots), a.tmp, x, L.nn);
-                    else if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM>(L, i, j, k, x, b, nullptr);
+                    else if (colour_slot(L.n1, c, t, i, j, k)) vel_uniform_node<T, FORM, false>(L, i, j, k, x, b, nullptr);
                 }
             }
             if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
@@ -465,8 +505,8 @@ __device__ __forceinline__ void uzawa_coop_body(const CoopArgs<T>& a) {
             // special rows first so that their quads stay aligned with the lanes
             for (long long t = tid; t < 4LL * np + slots; t += nth) {
                 int i, j, k;
-                if (t < 4LL * np) spec_row_quad<T, 2>(L, a.sp[c], np, a.cp[c], x, nullptr, g, t);
-                else if (colour_slot(L.n1, c, t - 4LL * np, i, j, k)) pre_uniform_node<T>(L, i, j, k, x, g);
+                if (t < 4LL * np) spec_row_quad<T, 2>(L, a.sp[c], a.cp[c], a.cft, x, nullptr, g, t);
+                else if (colour_slot(L.n1, c, t - 4LL * np, i, j, k)) pre_uniform_node<T, false>(L, i, j, k, x, g);
             }
             if (!phase_sync<CLUSTER>(a.bar, nb, a.err)) return;
         }
@@ -495,40 +535,28 @@ void count_launches(long long k) { g_launches.fetch_add(k, std::memory_order_rel
 long long launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 template <typename T>
-static const T* cf_full(const Level& L);
-template <> const double* cf_full<double>(const Level& L) { return L.cf_full_d; }
-template <> const float* cf_full<float>(const Level& L) { return L.cf_full_f; }
-template <typename T>
-static const T* cf_prow(const Level& L);
-template <> const double* cf_prow<double>(const Level& L) { return L.cf_prow_d; }
-template <> const float* cf_prow<float>(const Level& L) { return L.cf_prow_f; }
-template <typename T>
-static const T* cf_vel(const Level& L, int c);
-template <> const double* cf_vel<double>(const Level& L, int c) { return L.cf_vel_d[c]; }
-template <> const float* cf_vel<float>(const Level& L, int c) { return L.cf_vel_f[c]; }
-template <typename T>
-static const T* cf_pre(const Level& L, int c);
-template <> const double* cf_pre<double>(const Level& L, int c) { return L.cf_pre_d[c]; }
-template <> const float* cf_pre<float>(const Level& L, int c) { return L.cf_pre_f[c]; }
+static const T* cft(const Level& L);
+template <> const double* cft<double>(const Level& L) { return L.cft_d; }
+template <> const float* cft<float>(const Level& L) { return L.cft_f; }
 
 template <typename T>
 static void apply_form(const Hier& H, int l, const T* x, T* y, const T* b, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
-    count_launches(1 + (L.n_spec_full ? 1 : 0) + (L.n_spec_prow ? 1 : 0));
-    if (L.n_spec_full)
-        k_spec_rows<T, 0><<<blocks_for(4LL * (L.n_spec_full)), TPB, 0, s>>>(V, L.spec_full, L.n_spec_full, cf_full<T>(L), const_cast<T*>(x), y, b);
-    if (L.n_spec_prow)
-        k_spec_rows<T, 3><<<blocks_for(4LL * (L.n_spec_prow)), TPB, 0, s>>>(V, L.spec_prow, L.n_spec_prow, cf_prow<T>(L), const_cast<T*>(x), y, b);
+    count_launches(1 + (L.full.n ? 1 : 0) + (L.prow.n ? 1 : 0));
+    if (L.full.n)
+        launch_k(k_spec_rows<T, 0>, dim3(blocks_for(4LL * L.full.n)), dim3(TPB), s, V, L.full.node, L.full.cfg, L.full.n, cft<T>(L), const_cast<T*>(x), y, b);
+    if (L.prow.n)
+        launch_k(k_spec_rows<T, 3>, dim3(blocks_for(4LL * L.prow.n)), dim3(TPB), s, V, L.prow.node, L.prow.cfg, L.prow.n, cft<T>(L), const_cast<T*>(x), y, b);
     switch (L.form) {
         case FORM_SYM:
-            k_apply_uniform<T, FORM_SYM><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
+            launch_k(k_apply_uniform<T, FORM_SYM>, dim3(blocks_for(L.nn)), dim3(TPB), s, V, x, y, b);
             break;
         case FORM_GRAD:
-            k_apply_uniform<T, FORM_GRAD><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
+            launch_k(k_apply_uniform<T, FORM_GRAD>, dim3(blocks_for(L.nn)), dim3(TPB), s, V, x, y, b);
             break;
         default:
-            k_apply_uniform<T, FORM_TR><<<blocks_for(L.nn), TPB, 0, s>>>(V, x, y, b);
+            launch_k(k_apply_uniform<T, FORM_TR>, dim3(blocks_for(L.nn)), dim3(TPB), s, V, x, y, b);
     }
 }
 
@@ -540,21 +568,13 @@ void launch_apply(const Hier& H, int l, const T* x, T* y, const T* b, cudaStream
 template <int FORM>
 static void build_coefs_form(const Hier& H, int l, cudaStream_t s) {
     const Level& L = H.lv[l];
-    LevelView<double> V = view<double>(H, l);
-    auto run = [&](const int* list, int count, int r0, int nrow, bool diag, double* out, float* out_f, int ncoef) {
-        if (!count) return;
+    if (!L.n_cfg) return;
+    count_launches(1);
+    launch_k(k_build_cfg<FORM>, dim3(blocks_for(60LL * L.n_cfg)), dim3(TPB), s, view<double>(H, l), L.cfg_rep, L.n_cfg, L.cft_d);
+    if (L.cft_f) {
+        const long long m = (long long)CFG_STRIDE * L.n_cfg;
         count_launches(1);
-        k_build_coef<FORM><<<blocks_for(60LL * count), TPB, 0, s>>>(V, list, count, r0, nrow, diag, out);
-        if (out_f) {
-            count_launches(1);
-            k_d2f_plain<<<blocks_for((long long)ncoef * count), TPB, 0, s>>>(out_f, out, (long long)ncoef * count);
-        }
-    };
-    run(L.spec_full, L.n_spec_full, 0, 4, false, L.cf_full_d, L.cf_full_f, 240);
-    run(L.spec_prow, L.n_spec_prow, 3, 1, false, L.cf_prow_d, L.cf_prow_f, 60);
-    for (int c = 0; c < 2; ++c) {
-        run(L.spec_vel[c], L.n_spec_vel[c], 0, 3, true, L.cf_vel_d[c], L.cf_vel_f[c], 183);
-        run(L.spec_pre[c], L.n_spec_pre[c], 3, 1, true, L.cf_pre_d[c], L.cf_pre_f[c], 61);
+        launch_k(k_d2f_plain, dim3(blocks_for(m)), dim3(TPB), s, L.cft_f, L.cft_d, m);
     }
 }
 
@@ -586,17 +606,19 @@ static void velocity_pass(const Hier& H, int l, int colour, T* x, const T* f, cu
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
     const long long slots = colour_slots(L.n + 1);
-    const int cnt = L.n_spec_vel[colour];
-    const int* list = L.spec_vel[colour];
+    const int cnt = L.vel[colour].n;
+    const int* list = L.vel[colour].node;
     T* tmp = spec_scratch<T>(L);
-    count_launches((FORM == FORM_SYM ? 2 : 1) + (cnt ? 1 : 0));
-    if (cnt) k_spec_rows<T, 1><<<blocks_for(4LL * cnt), TPB, 0, s>>>(V, list, cnt, cf_vel<T>(L, colour), x, tmp, f);
     if (FORM == FORM_SYM) {
         T* out = sym_scratch<T>(L);
-        k_vel_uniform<T, FORM><<<blocks_for(slots, CTPB), CTPB, 0, s>>>(V, colour, x, f, out, list, 0, tmp);
-        k_vel_copy_colour<T><<<blocks_for(slots + cnt, CTPB), CTPB, 0, s>>>(V, colour, out, x, list, cnt, tmp);
+        count_launches(2);
+        launch_k(k_vel_sym_stage<T>, dim3(blocks_for(4LL * cnt + slots, CTPB)), dim3(CTPB), s, V, colour, (const T*)x, f,
+                 out, list, L.vel[colour].cfg, cnt, cft<T>(L), tmp);
+        launch_k(k_vel_copy_colour<T>, dim3(blocks_for(slots + cnt, CTPB)), dim3(CTPB), s, V, colour, out, x, list, cnt, tmp);
     } else {
-        k_vel_uniform<T, FORM><<<blocks_for(slots + cnt, CTPB), CTPB, 0, s>>>(V, colour, x, f, nullptr, list, cnt, tmp);
+        count_launches(1 + (cnt ? 1 : 0));
+        if (cnt) launch_k(k_spec_rows<T, 1>, dim3(blocks_for(4LL * cnt)), dim3(TPB), s, V, list, L.vel[colour].cfg, cnt, cft<T>(L), x, tmp, f);
+        launch_k(k_vel_uniform<T, FORM>, dim3(blocks_for(slots + cnt, CTPB)), dim3(CTPB), s, V, colour, x, f, nullptr, list, cnt, tmp);
     }
 }
 
@@ -605,10 +627,10 @@ static void pressure_pass(const Hier& H, int l, int colour, T* x, const T* g, cu
     const Level& L = H.lv[l];
     LevelView<T> V = view<T>(H, l);
     const long long slots = colour_slots(L.n + 1);
-    const int cnt = L.n_spec_pre[colour];
+    const int cnt = L.pre[colour].n;
     count_launches(1);
-    k_pre_uniform<T><<<blocks_for(4LL * cnt + slots, CTPB), CTPB, 0, s>>>(V, colour, x, g, L.spec_pre[colour], cnt,
-                                                                          cf_pre<T>(L, colour));
+    launch_k(k_pre_uniform<T>, dim3(blocks_for(4LL * cnt + slots, CTPB)), dim3(CTPB), s, V, colour, x, g, L.pre[colour].node,
+                                                                          L.pre[colour].cfg, cnt, cft<T>(L));
 }
 
 template <typename T>
@@ -635,9 +657,10 @@ static CoopArgs<T> coop_args(const Hier& H, int l, T* x, const T* b, int steps) 
     a.b = b;
     a.steps = steps;
     for (int c = 0; c < 2; ++c) {
-        a.sv[c] = L.spec_vel[c]; a.cv[c] = cf_vel<T>(L, c); a.nv[c] = L.n_spec_vel[c];
-        a.sp[c] = L.spec_pre[c]; a.cp[c] = cf_pre<T>(L, c); a.np[c] = L.n_spec_pre[c];
+        a.sv[c] = L.vel[c].node; a.cv[c] = L.vel[c].cfg; a.nv[c] = L.vel[c].n;
+        a.sp[c] = L.pre[c].node; a.cp[c] = L.pre[c].cfg; a.np[c] = L.pre[c].n;
     }
+    a.cft = cft<T>(L);
     a.tmp = spec_scratch<T>(L);
     a.sym = sym_scratch<T>(L);
     a.bar = H.coop_bar;
@@ -662,8 +685,7 @@ static bool uzawa_coop(const Hier& H, int l, T* x, const T* b, int steps, cudaSt
     }
     if (per_sm < 1) return false;
     const long long slots = colour_slots(L.n + 1);
-    const long long work = slots + std::max(std::max(L.n_spec_vel[0], L.n_spec_vel[1]),
-                                            std::max(L.n_spec_pre[0], L.n_spec_pre[1]));
+    const long long work = slots + std::max(std::max(L.vel[0].n, L.vel[1].n), std::max(L.pre[0].n, L.pre[1].n));
     // at least one block per SM: a phase of a small level is bound by the FP64 rate of the SMs
     // that hold its work, not by the number of items
     const long long want = std::max<long long>((work + COOP_TPB - 1) / COOP_TPB, sms);
@@ -727,8 +749,10 @@ static bool uzawa_cluster(const Hier& H, int l, T* x, const T* b, int steps, cud
 template <typename T>
 void launch_uzawa_steps(const Hier& H, int l, T* x, const T* b, int steps, cudaStream_t s) {
     const Level& L = H.lv[l];
-    // (FP64 phases on one GPC are bound by its FP64 rate: the cluster path is for FP32 cycles)
-    if (sizeof(T) == 4 && steps > 0 && H.use_coop && L.nn <= H.cluster_max_nodes) {
+    // FP64 phases on one GPC are bound by its FP64 rate, so FP64 levels have their own (smaller)
+    // limit for the cluster path
+    const long long cmax = sizeof(T) == 4 ? H.cluster_max_nodes : H.cluster_max_nodes64;
+    if (steps > 0 && H.use_coop && L.nn <= cmax) {
         bool ok = false;
         switch (L.form) {
             case FORM_SYM: ok = uzawa_cluster<T, FORM_SYM>(H, l, x, b, steps, s); break;
@@ -766,69 +790,92 @@ void launch_smooth_pass(const Hier& H, int l, int which, int colour, T* x, const
 template <typename T>
 void launch_restrict(const Hier& H, int l, const T* rf, T* bc, cudaStream_t s) {
     count_launches(1);
-    k_restrict<T><<<blocks_for(H.lv[l + 1].nn), TPB, 0, s>>>(view<T>(H, l), view<T>(H, l + 1), rf, bc);
+    launch_k(k_restrict<T>, dim3(blocks_for(H.lv[l + 1].nn)), dim3(TPB), s, view<T>(H, l), view<T>(H, l + 1), rf, bc);
 }
 
 template <typename T>
 void launch_prolong_add(const Hier& H, int l, const T* ec, T* xf, cudaStream_t s) {
     count_launches(1);
-    k_prolong_add<T><<<blocks_for(H.lv[l].nn), TPB, 0, s>>>(view<T>(H, l), view<T>(H, l + 1), ec, xf);
+    launch_k(k_prolong_add<T>, dim3(blocks_for(H.lv[l].nn)), dim3(TPB), s, view<T>(H, l), view<T>(H, l + 1), ec, xf);
 }
 
 void launch_rhs(const Hier& H, const double* f, double* b, cudaStream_t s) {
     count_launches(1);
-    k_rhs<<<blocks_for(H.lv[0].nn), TPB, 0, s>>>(view<double>(H, 0), f, b);
+    launch_k(k_rhs, dim3(blocks_for(H.lv[0].nn)), dim3(TPB), s, view<double>(H, 0), f, b);
 }
 
 template <typename T>
 void vec_zero(T* v, long long count, cudaStream_t s) {
     count_launches(1);
-    k_zero<T><<<blocks_for(count), TPB, 0, s>>>(v, count);
+    launch_k(k_zero<T>, dim3(blocks_for(count)), dim3(TPB), s, v, count);
 }
 void vec_axpy_dev(double* y, const double* x, const double* a, double sign, long long count, cudaStream_t s) {
     count_launches(1);
-    k_axpy_dev<<<blocks_for(count), TPB, 0, s>>>(y, x, a, sign, count);
+    launch_k(k_axpy_dev, dim3(blocks_for(count)), dim3(TPB), s, y, x, a, sign, count);
 }
 void vec_axpy(double* y, const double* x, double a, long long count, cudaStream_t s) {
     count_launches(1);
-    k_axpy<<<blocks_for(count), TPB, 0, s>>>(y, x, a, count);
+    launch_k(k_axpy, dim3(blocks_for(count)), dim3(TPB), s, y, x, a, count);
 }
 void vec_scale_dev(double* y, const double* x, const double* sc, bool recip, long long count, cudaStream_t s) {
     count_launches(1);
-    k_scale_dev<<<blocks_for(count), TPB, 0, s>>>(y, x, sc, recip, count);
+    launch_k(k_scale_dev, dim3(blocks_for(count)), dim3(TPB), s, y, x, sc, recip, count);
 }
 void vec_copy(double* y, const double* x, long long count, cudaStream_t s) {
     count_launches(1);
-    k_copy<<<blocks_for(count), TPB, 0, s>>>(y, x, count);
+    launch_k(k_copy, dim3(blocks_for(count)), dim3(TPB), s, y, x, count);
 }
 void vec_d2f(float* y, const double* x, const double* sc, long long count, cudaStream_t s) {
     count_launches(1);
-    k_d2f<<<blocks_for(count), TPB, 0, s>>>(y, x, sc, count);
+    launch_k(k_d2f, dim3(blocks_for(count)), dim3(TPB), s, y, x, sc, count);
 }
 void vec_f2d_add(double* y, const float* x, const double* sc, long long count, cudaStream_t s) {
     count_launches(1);
-    k_f2d_add<<<blocks_for(count), TPB, 0, s>>>(y, x, sc, count);
+    launch_k(k_f2d_add, dim3(blocks_for(count)), dim3(TPB), s, y, x, sc, count);
 }
 void vec_f2d(double* y, const float* x, const double* sc, long long count, cudaStream_t s) {
     count_launches(1);
-    k_f2d<<<blocks_for(count), TPB, 0, s>>>(y, x, sc, count);
+    launch_k(k_f2d, dim3(blocks_for(count)), dim3(TPB), s, y, x, sc, count);
 }
 void vec_dot(const Hier& H, const double* x, const double* y, long long count, double* out, cudaStream_t s) {
     int blocks = (int)std::min<long long>(H.red_blocks, (count + RED_TPB - 1) / RED_TPB);
     if (blocks < 1) blocks = 1;
     count_launches(2);
-    k_dot_part<<<blocks, RED_TPB, 0, s>>>(x, y, count, H.red_part);
-    k_dot_final<<<1, 1024, 0, s>>>(H.red_part, blocks, out);
+    launch_k(k_dot_part, dim3(blocks), dim3(RED_TPB), s, x, y, count, H.red_part);
+    launch_k(k_dot_final, dim3(1), dim3(1024), s, H.red_part, blocks, out);
 }
 
 template <typename T>
 void launch_coarse_solve(const Hier& H, const T* b, T* x, cudaStream_t s) {
     const Coarse& C = H.coarse;
     count_launches(3);
-    k_gather_free<T><<<blocks_for(C.nf), TPB, 0, s>>>(C.free_idx, C.nf, b, C.bc);
-    k_dense_mv<<<blocks_for((long long)C.nf * 32), TPB, 0, s>>>(C.kinv, C.nf, C.bc, C.xc);
+    launch_k(k_gather_free<T>, dim3(blocks_for(C.nf)), dim3(TPB), s, C.free_idx, C.nf, b, C.bc);
+    launch_k(k_dense_mv, dim3(blocks_for((long long)C.nf * 32)), dim3(TPB), s, C.kinv, C.nf, C.bc, C.xc);
     vec_zero<T>(x, 4 * H.lv.back().nn, s);
-    k_scatter_free<T><<<blocks_for(C.nf), TPB, 0, s>>>(C.free_idx, C.nf, C.xc, x);
+    launch_k(k_scatter_free<T>, dim3(blocks_for(C.nf)), dim3(TPB), s, C.free_idx, C.nf, C.xc, x);
+}
+
+namespace {
+__global__ void k_fold_correction(double* __restrict__ kinv, int nf, int nu, const int* __restrict__ colptr,
+                                  const int* __restrict__ rows, const double* __restrict__ vals) {
+    pdl_prologue();
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long np = nf - nu;
+    if (t >= (long long)nf * np) return;
+    const long long i = t / np;
+    const int c = (int)(t - i * np);
+    double* row = kinv + i * nf;
+    double acc = row[nu + c];
+    for (int k = colptr[c]; k < colptr[c + 1]; ++k) acc += row[rows[k]] * vals[k];
+    row[nu + c] = acc;  // reads only velocity columns (rows[k] < nu): in place is safe
+}
+}  // namespace
+
+void fold_coarse_correction(double* kinv, int nf, int nu, const int* colptr, const int* rows,
+                            const double* vals, cudaStream_t s) {
+    if (nf <= nu) return;
+    count_launches(1);
+    launch_k(k_fold_correction, dim3(blocks_for((long long)nf * (nf - nu))), dim3(TPB), s, kinv, nf, nu, colptr, rows, vals);
 }
 
 bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s) {
@@ -840,14 +887,14 @@ bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s) {
     if (cudaMalloc(&status, sizeof(int)) != cudaSuccess) { cudaFree(aug); cudaFree(col); return false; }
     cudaMemsetAsync(status, 0, sizeof(int), s);
     count_launches(2 + 3LL * n);
-    k_gj_init<<<blocks_for((long long)n * 2 * n), TPB, 0, s>>>(aug, a_dev, n);
+    launch_k(k_gj_init, dim3(blocks_for((long long)n * 2 * n)), dim3(TPB), s, aug, a_dev, n);
     dim3 eg(blocks_for(2 * n), n);
     for (int k = 0; k < n; ++k) {
-        k_gj_pivot<<<1, 1024, 0, s>>>(aug, n, k, status);
-        k_gj_col<<<blocks_for(n), TPB, 0, s>>>(aug, n, k, col);
-        k_gj_elim<<<eg, TPB, 0, s>>>(aug, n, k, col);
+        launch_k(k_gj_pivot, dim3(1), dim3(1024), s, aug, n, k, status);
+        launch_k(k_gj_col, dim3(blocks_for(n)), dim3(TPB), s, aug, n, k, col);
+        launch_k(k_gj_elim, dim3(eg), dim3(TPB), s, aug, n, k, col);
     }
-    k_gj_extract<<<blocks_for((long long)n * n), TPB, 0, s>>>(aug, n, inv_dev);
+    launch_k(k_gj_extract, dim3(blocks_for((long long)n * n)), dim3(TPB), s, aug, n, inv_dev);
     int st = 0;
     cudaMemcpyAsync(&st, status, sizeof(int), cudaMemcpyDeviceToHost, s);
     cudaStreamSynchronize(s);
@@ -892,11 +939,11 @@ static void velocity_pass_static(const Hier& H, int l, int colour, double* x, co
                                  double* tmp, cudaStream_t s) {
     const Level& L = H.lv[l];
     LevelView<double> V = view<double>(H, l);
-    const int cnt = L.n_spec_vel[colour];
+    const int cnt = L.vel[colour].n;
     count_launches(1 + (cnt ? 1 : 0));
-    if (cnt) k_spec_rows<double, 1><<<blocks_for(4LL * (cnt)), TPB, 0, s>>>(V, L.spec_vel[colour], cnt, L.cf_vel_d[colour], x, tmp, f);
-    k_vel_uniform<double, FORM><<<blocks_for(colour_slots(L.n + 1) + cnt, CTPB), CTPB, 0, s>>>(
-        V, colour, x, f, nullptr, L.spec_vel[colour], cnt, tmp);
+    if (cnt) launch_k(k_spec_rows<double, 1>, dim3(blocks_for(4LL * cnt)), dim3(TPB), s, V, L.vel[colour].node, L.vel[colour].cfg, cnt, L.cft_d, x, tmp, f);
+    launch_k(k_vel_uniform<double, FORM>, dim3(blocks_for(colour_slots(L.n + 1) + cnt, CTPB)), dim3(CTPB), s, 
+        V, colour, x, f, nullptr, L.vel[colour].node, cnt, tmp);
 }
 
 int launch_velocity_pass_noalloc(const Hier& H, int l, int colour, double* x, const double* b,
@@ -907,8 +954,8 @@ int launch_velocity_pass_noalloc(const Hier& H, int l, int colour, double* x, co
               "vector; use sdx_smooth_pass";
         return -1;
     }
-    if (L.n_spec_vel[colour] > NOALLOC_MAX_ROWS) {
-        err = "sdx_smooth_pass_noalloc: " + std::to_string(L.n_spec_vel[colour]) +
+    if (L.vel[colour].n > NOALLOC_MAX_ROWS) {
+        err = "sdx_smooth_pass_noalloc: " + std::to_string(L.vel[colour].n) +
               " boundary/interface rows in this colour exceed the fixed maximum of " +
               std::to_string(NOALLOC_MAX_ROWS);
         return -1;

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
@@ -18,13 +19,28 @@ namespace sdx {
 static thread_local std::string g_last_error = "no error";
 void set_error(const std::string& msg) { g_last_error = msg; }
 
+bool pdl_enabled() {
+    static const bool on = [] {
+        const char* e = std::getenv("SDX_NO_PDL");
+        return !(e && e[0] == '1');
+    }();
+    return on;
+}
+
+template <typename T>
+static void set_tables(LevelView<T>& v, const T* tab, double h) {
+    v.muh = tab; v.idA = tab + 256; v.tauh = tab + 512; v.idC = tab + 768;
+    v.a1 = tab + 1024; v.a2 = tab + 1280; v.a3 = tab + 1536; v.k12 = tab + 1792;
+    v.h2_3 = (T)(h * h / 3.0); v.h2_6 = (T)(h * h / 6.0); v.h2_12 = (T)(h * h / 12.0);
+}
+
 template <>
 LevelView<double> view<double>(const Hier& H, int l) {
     const Level& L = H.lv[l];
     LevelView<double> v;
     v.n = L.n; v.n1 = L.n + 1; v.nn = L.nn; v.s1 = L.n + 1; v.s2 = (long long)(L.n + 1) * (L.n + 1);
     v.P = L.n + 2; v.h = L.h; v.cid = L.cid; v.info = L.info; v.mu = H.mu_d; v.tau = L.tau_d;
-    v.muh = L.tab_d; v.idA = L.tab_d + 256; v.tauh = L.tab_d + 512; v.idC = L.tab_d + 768;
+    set_tables(v, L.tab_d, L.h);
     return v;
 }
 template <>
@@ -33,7 +49,7 @@ LevelView<float> view<float>(const Hier& H, int l) {
     LevelView<float> v;
     v.n = L.n; v.n1 = L.n + 1; v.nn = L.nn; v.s1 = L.n + 1; v.s2 = (long long)(L.n + 1) * (L.n + 1);
     v.P = L.n + 2; v.h = (float)L.h; v.cid = L.cid; v.info = L.info; v.mu = H.mu_f; v.tau = L.tau_f;
-    v.muh = L.tab_f; v.idA = L.tab_f + 256; v.tauh = L.tab_f + 512; v.idC = L.tab_f + 768;
+    set_tables(v, L.tab_f, L.h);
     return v;
 }
 
@@ -83,23 +99,47 @@ static void build_level_host(const Hier& H, Level& L, const std::vector<uint8_t>
     L.free_dofs = free_dofs;
 }
 
+// Special rows of a level with their stencil configurations.  A configuration is the key
+// (ids of the eight cells around the node, ghost cells included; interface flag): the row's
+// coefficients are sums over the 24 tetrahedra in those cells, so equal keys give equal
+// coefficients, and one representative node per key is enough to evaluate them.
 static void upload_level(Hier& H, Level& L) {
-    const int n1 = L.n + 1;
-    std::vector<int> all, full, prow, vel[2], pre[2];
+    const int n1 = L.n + 1, P = L.n + 2;
+    std::vector<int> full[2], prow[2], vel[2][2], pre[2][2];  // [0] nodes, [1] configurations
+    std::map<std::pair<uint64_t, uint16_t>, int> cfg_of;
+    std::vector<int> reps;
     for (int k = 0; k < n1; ++k)
         for (int j = 0; j < n1; ++j)
             for (int i = 0; i < n1; ++i) {
                 const int node = i + n1 * (j + n1 * k);
                 const uint16_t inf = L.info_host[node];
                 if (!(inf & INFO_SPECIAL)) continue;
-                const int c = (i + j + k) & 1;
-                all.push_back(node);
-                pre[c].push_back(node);
-                if ((inf & 7) != 7) {
-                    vel[c].push_back(node);
-                    full.push_back(node);
+                uint64_t cells = 0;
+                for (int q = 0; q < 8; ++q) {
+                    const int ox = i - (q & 1), oy = j - ((q >> 1) & 1), oz = k - ((q >> 2) & 1);
+                    cells |= (uint64_t)L.cid_host[(ox + 1) + (size_t)P * ((oy + 1) + (size_t)P * (oz + 1))] << (8 * q);
+                }
+                const auto key = std::make_pair(cells, (uint16_t)(inf & INFO_IFACE));
+                auto it = cfg_of.find(key);
+                int cfg;
+                if (it == cfg_of.end()) {
+                    cfg = (int)reps.size();
+                    cfg_of.emplace(key, cfg);
+                    reps.push_back(node);
                 } else {
-                    prow.push_back(node);
+                    cfg = it->second;
+                }
+                const int c = (i + j + k) & 1;
+                pre[c][0].push_back(node);
+                pre[c][1].push_back(cfg);
+                if ((inf & 7) != 7) {
+                    vel[c][0].push_back(node);
+                    vel[c][1].push_back(cfg);
+                    full[0].push_back(node);
+                    full[1].push_back(cfg);
+                } else {
+                    prow[0].push_back(node);
+                    prow[1].push_back(cfg);
                 }
             }
     const size_t P3 = L.cid_host.size();
@@ -107,18 +147,24 @@ static void upload_level(Hier& H, Level& L) {
     CK(cudaMemcpy(L.cid, L.cid_host.data(), P3, cudaMemcpyHostToDevice));
     L.info = dalloc<uint16_t>(L.nn);
     CK(cudaMemcpy(L.info, L.info_host.data(), sizeof(uint16_t) * L.nn, cudaMemcpyHostToDevice));
-    auto up = [](const std::vector<int>& v, int*& d, int& cnt) {
-        cnt = (int)v.size();
-        d = dalloc<int>(cnt);
-        if (cnt) CK(cudaMemcpy(d, v.data(), sizeof(int) * cnt, cudaMemcpyHostToDevice));
+    auto up = [](const std::vector<int>& v) {
+        int* d = dalloc<int>((long long)v.size());
+        if (!v.empty()) CK(cudaMemcpy(d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+        return d;
     };
-    up(all, L.spec_all, L.n_spec_all);
-    up(full, L.spec_full, L.n_spec_full);
-    up(prow, L.spec_prow, L.n_spec_prow);
+    auto up_rows = [&](std::vector<int>* src, SpecRows& dst) {
+        dst.n = (int)src[0].size();
+        dst.node = up(src[0]);
+        dst.cfg = up(src[1]);
+    };
+    up_rows(full, L.full);
+    up_rows(prow, L.prow);
     for (int c = 0; c < 2; ++c) {
-        up(vel[c], L.spec_vel[c], L.n_spec_vel[c]);
-        up(pre[c], L.spec_pre[c], L.n_spec_pre[c]);
+        up_rows(vel[c], L.vel[c]);
+        up_rows(pre[c], L.pre[c]);
     }
+    L.n_cfg = (int)reps.size();
+    L.cfg_rep = up(reps);
     std::vector<double> tau(256, 0.0);
     std::vector<float> tauf(256, 0.0f);
     for (int id = 0; id < 255; ++id)
@@ -131,22 +177,28 @@ static void upload_level(Hier& H, Level& L) {
     CK(cudaMemcpy(L.tau_d, tau.data(), sizeof(double) * 256, cudaMemcpyHostToDevice));
     CK(cudaMemcpy(L.tau_f, tauf.data(), sizeof(float) * 256, cudaMemcpyHostToDevice));
     // per-id constants of uniform nodes (diagonals are sums over the 24 tetrahedra around a node)
-    std::vector<double> tab(4 * 256, 0.0);
-    std::vector<float> tabf(4 * 256, 0.0f);
+    std::vector<double> tab(NTAB * 256, 0.0);
+    std::vector<float> tabf(NTAB * 256, 0.0f);
     const double dA = L.form == FORM_SYM ? 8.0 : 6.0;
+    const double h2 = L.h * L.h;
     for (int id = 0; id < 255; ++id)
         if (H.mu_table[id] > 0) {
             const double muh = H.mu_table[id] * L.h, tauh = tau[id] * L.h;
+            const double ida = 1.0 / (dA * muh), idc = OMEGA / (6.0 * tauh);
             tab[id] = muh;
-            tab[256 + id] = 1.0 / (dA * muh);
+            tab[256 + id] = ida;
             tab[512 + id] = tauh;
-            tab[768 + id] = OMEGA / (6.0 * tauh);
+            tab[768 + id] = idc;
+            tab[1024 + id] = ida * h2 / 3.0;
+            tab[1280 + id] = -ida * h2 / 6.0;
+            tab[1536 + id] = ida * h2 / 12.0;
+            tab[1792 + id] = idc * h2 / 12.0;
         }
-    for (int i = 0; i < 4 * 256; ++i) tabf[i] = (float)tab[i];
-    L.tab_d = dalloc<double>(4 * 256);
-    L.tab_f = dalloc<float>(4 * 256);
-    CK(cudaMemcpy(L.tab_d, tab.data(), sizeof(double) * 4 * 256, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(L.tab_f, tabf.data(), sizeof(float) * 4 * 256, cudaMemcpyHostToDevice));
+    for (int i = 0; i < NTAB * 256; ++i) tabf[i] = (float)tab[i];
+    L.tab_d = dalloc<double>(NTAB * 256);
+    L.tab_f = dalloc<float>(NTAB * 256);
+    CK(cudaMemcpy(L.tab_d, tab.data(), sizeof(double) * NTAB * 256, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(L.tab_f, tabf.data(), sizeof(float) * NTAB * 256, cudaMemcpyHostToDevice));
     const long long v4 = 4 * L.nn;
     L.x = dalloc<double>(v4);
     L.b = dalloc<double>(v4);
@@ -161,24 +213,11 @@ static void upload_level(Hier& H, Level& L) {
         L.sym_tmp = dalloc<double>(3 * L.nn);
         if (H.prec == SDX_PREC_FP32_REFINED) L.sym_tmp32 = dalloc<float>(3 * L.nn);
     }
-    const int mx = std::max(L.n_spec_vel[0], L.n_spec_vel[1]);
+    const int mx = std::max(L.vel[0].n, L.vel[1].n);
     L.spec_tmp = dalloc<double>(3LL * mx);
     if (H.prec == SDX_PREC_FP32_REFINED) L.spec_tmp32 = dalloc<float>(3LL * mx);
-    const bool f32 = H.prec == SDX_PREC_FP32_REFINED;
-    L.cf_full_d = dalloc<double>(240LL * L.n_spec_full);
-    L.cf_prow_d = dalloc<double>(60LL * L.n_spec_prow);
-    if (f32) {
-        L.cf_full_f = dalloc<float>(240LL * L.n_spec_full);
-        L.cf_prow_f = dalloc<float>(60LL * L.n_spec_prow);
-    }
-    for (int c = 0; c < 2; ++c) {
-        L.cf_vel_d[c] = dalloc<double>(183LL * L.n_spec_vel[c]);
-        L.cf_pre_d[c] = dalloc<double>(61LL * L.n_spec_pre[c]);
-        if (f32) {
-            L.cf_vel_f[c] = dalloc<float>(183LL * L.n_spec_vel[c]);
-            L.cf_pre_f[c] = dalloc<float>(61LL * L.n_spec_pre[c]);
-        }
-    }
+    L.cft_d = dalloc<double>((long long)CFG_STRIDE * L.n_cfg);
+    if (H.prec == SDX_PREC_FP32_REFINED) L.cft_f = dalloc<float>((long long)CFG_STRIDE * L.n_cfg);
 }
 
 // Coarsest-grid saddle matrix by probing with the device apply: the 27 node classes
@@ -279,6 +318,51 @@ static void build_coarse(Hier& H) {
     CK(cudaMemcpy2D(C.kinv, sizeof(double) * nf, Minv, sizeof(double) * nb, sizeof(double) * nf, nf,
                     cudaMemcpyDeviceToDevice));
     cudaFree(Minv);
+    if (H.coarse_correction) {
+        // Sec. 5 coarse-grid variant: the solve takes b + E b with E b = (B^T D b_p) on the free
+        // velocity rows, D_a = mu_a / m_a (m_a = int lambda_a, mu_a m_a = int mu lambda_a), so
+        // the inverse becomes Kinv (I + E); E has entries only in (velocity row, pressure column)
+        // and B^T is the upper-right block of the probed matrix M.
+        const int P = L.n + 2;
+        const double h3 = L.h * L.h * L.h;
+        int nu = 0;
+        while (nu < nf && free_idx[nu] < 3 * nn) ++nu;
+        std::vector<int> colptr(1, 0), rows;
+        std::vector<double> vals;
+        for (int cp = nu; cp < nf; ++cp) {
+            const long long node = free_idx[cp] - 3 * nn;
+            const int i = (int)(node % n1), j = (int)((node / n1) % n1), k = (int)(node / ((long long)n1 * n1));
+            double m = 0, mum = 0;
+            for (int q = 0; q < 8; ++q) {
+                const int qx = q & 1, qy = (q >> 1) & 1, qz = (q >> 2) & 1;
+                const uint8_t id = L.cid_host[(i - qx + 1) + (size_t)P * ((j - qy + 1) + (size_t)P * (k - qz + 1))];
+                if (id == CELL_OUTSIDE) continue;
+                const double w = ((q == 0 || q == 7) ? 6 : 2) * h3 / 24.0;  // tetrahedra of the cell at the node x |T|/4
+                m += w;
+                mum += w * H.mu_table[id];
+            }
+            const double D = mum / (m * m);
+            for (int r = 0; r < nu; ++r) {
+                const double bt = M[(size_t)r * nb + cp];
+                if (bt != 0.0) { rows.push_back(r); vals.push_back(bt * D); }
+            }
+            colptr.push_back((int)rows.size());
+        }
+        int* colptr_d = dalloc<int>((long long)colptr.size());
+        int* rows_d = dalloc<int>((long long)rows.size());
+        double* vals_d = dalloc<double>((long long)vals.size());
+        CK(cudaMemcpy(colptr_d, colptr.data(), sizeof(int) * colptr.size(), cudaMemcpyHostToDevice));
+        if (!rows.empty()) {
+            CK(cudaMemcpy(rows_d, rows.data(), sizeof(int) * rows.size(), cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(vals_d, vals.data(), sizeof(double) * vals.size(), cudaMemcpyHostToDevice));
+        }
+        fold_coarse_correction(C.kinv, nf, nu, colptr_d, rows_d, vals_d, 0);
+        const cudaError_t e = cudaDeviceSynchronize();
+        cudaFree(colptr_d);
+        cudaFree(rows_d);
+        cudaFree(vals_d);
+        CK(e);
+    }
     C.bc = dalloc<double>(nf);
     C.xc = dalloc<double>(nf);
     CK(cudaMemset(L.x, 0, sizeof(double) * 4 * nn));
@@ -288,14 +372,13 @@ void hier_free(Hier* H) {
     if (!H) return;
     cudaDeviceSynchronize();
     for (Level& L : H->lv) {
-        void* cfs[] = {L.spec_full, L.spec_prow, L.cf_full_d, L.cf_full_f, L.cf_prow_d, L.cf_prow_f,
-                       L.cf_vel_d[0], L.cf_vel_d[1], L.cf_vel_f[0], L.cf_vel_f[1],
-                       L.cf_pre_d[0], L.cf_pre_d[1], L.cf_pre_f[0], L.cf_pre_f[1]};
-        for (void* p : cfs)
-            if (p) cudaFree(p);
-        void* ptrs[] = {L.cid, L.info, L.tau_d, L.tau_f, L.tab_d, L.tab_f, L.spec_all, L.spec_vel[0], L.spec_vel[1],
-                        L.spec_pre[0], L.spec_pre[1], L.x, L.b, L.r, L.x32, L.b32, L.r32,
-                        L.sym_tmp, L.sym_tmp32, L.spec_tmp, L.spec_tmp32};
+        const SpecRows* rows[] = {&L.full, &L.prow, &L.vel[0], &L.vel[1], &L.pre[0], &L.pre[1]};
+        for (const SpecRows* r : rows) {
+            if (r->node) cudaFree(r->node);
+            if (r->cfg) cudaFree(r->cfg);
+        }
+        void* ptrs[] = {L.cid, L.info, L.tau_d, L.tau_f, L.tab_d, L.tab_f, L.cft_d, L.cft_f, L.cfg_rep,
+                        L.x, L.b, L.r, L.x32, L.b32, L.r32, L.sym_tmp, L.sym_tmp32, L.spec_tmp, L.spec_tmp32};
         for (void* p : ptrs)
             if (p) cudaFree(p);
     }
@@ -327,7 +410,14 @@ Hier* hier_create(const sdx_desc* d) {
         if (!(d->mu[i] > 0) || !std::isfinite(d->mu[i])) { set_error("viscosities must be finite and > 0"); throw Fail{SDX_EINVAL}; }
     for (int f = 0; f < 6; ++f)
         if (d->face[f] < 0 || d->face[f] > 2) { set_error("invalid face type"); throw Fail{SDX_EINVAL}; }
-    if (d->form < 0 || d->form > 2 || d->coarse_form < -1 || d->coarse_form > 2) { set_error("invalid form"); throw Fail{SDX_EINVAL}; }
+    if (d->form < 0 || d->form > 2 || d->coarse_form < -1 || d->coarse_form > 2 || d->coarsest_form < -1 ||
+        d->coarsest_form > 2) { set_error("invalid form"); throw Fail{SDX_EINVAL}; }
+    if (d->coarse_correction != 0 && d->coarse_correction != 1) { set_error("coarse_correction must be 0 or 1"); throw Fail{SDX_EINVAL}; }
+    if (d->coarsening != 0 && d->coarsening != 1) { set_error("coarsening must be 0 or 1"); throw Fail{SDX_EINVAL}; }
+    if (d->coarse_correction && (d->n == d->n_coarse || d->coarsest_form != FORM_SYM)) {
+        set_error("coarse_correction needs at least two levels and coarsest_form = SDX_FORM_STRAIN");
+        throw Fail{SDX_EINVAL};
+    }
     if (d->prec != SDX_PREC_FP64 && d->prec != SDX_PREC_FP32_REFINED) { set_error("invalid precision"); throw Fail{SDX_EINVAL}; }
     if (!(d->pspg_beta > 0) || !std::isfinite(d->pspg_beta)) { set_error("pspg_beta must be > 0"); throw Fail{SDX_EINVAL}; }
     const long long n3 = (long long)d->n * d->n * d->n;
@@ -339,6 +429,8 @@ Hier* hier_create(const sdx_desc* d) {
     try {
         H->n = d->n; H->n_coarse = d->n_coarse; H->prec = d->prec; H->beta = d->pspg_beta;
         H->form = d->form; H->coarse_form = d->coarse_form < 0 ? d->form : d->coarse_form;
+        H->coarsest_form = d->coarsest_form < 0 ? H->coarse_form : d->coarsest_form;
+        H->coarse_correction = d->coarse_correction == 1;
         bool traction = false;
         for (int f = 0; f < 6; ++f) { H->face[f] = d->face[f]; traction |= d->face[f] == SDX_FACE_TRACTION; }
         H->nullspace = !traction;
@@ -358,7 +450,7 @@ Hier* hier_create(const sdx_desc* d) {
             H->lv.emplace_back();
             Level& L = H->lv.back();
             L.n = m;
-            L.form = lvl == 0 ? H->form : H->coarse_form;
+            L.form = lvl == 0 ? H->form : (m == d->n_coarse ? H->coarsest_form : H->coarse_form);
             build_level_host(*H, L, cells);
             if (m == d->n_coarse) break;
             const int mc = m / 2;
@@ -366,15 +458,31 @@ Hier* hier_create(const sdx_desc* d) {
             for (int k = 0; k < mc; ++k)
                 for (int j = 0; j < mc; ++j)
                     for (int i = 0; i < mc; ++i) {
-                        const uint8_t id0 = cells[2 * i + (size_t)m * (2 * j + (size_t)m * 2 * k)];
-                        for (int q = 1; q < 8; ++q) {
-                            const uint8_t id = cells[(2 * i + (q & 1)) + (size_t)m * ((2 * j + ((q >> 1) & 1)) + (size_t)m * (2 * k + ((q >> 2) & 1)))];
-                            if (H->mu_table[id] != H->mu_table[id0]) {
-                                set_error("viscosity interface not resolved on the coarser grids");
-                                throw Fail{SDX_EINVAL};
+                        uint8_t kid[8];
+                        for (int q = 0; q < 8; ++q)
+                            kid[q] = cells[(2 * i + (q & 1)) + (size_t)m * ((2 * j + ((q >> 1) & 1)) + (size_t)m * (2 * k + ((q >> 2) & 1)))];
+                        uint8_t id = kid[0];
+                        if (d->coarsening == 0) {
+                            for (int q = 1; q < 8; ++q)
+                                if (H->mu_table[kid[q]] != H->mu_table[kid[0]]) {
+                                    set_error("viscosity interface not resolved on the coarser grids "
+                                              "(coarsening = 1 accepts interfaces the coarse grids cut)");
+                                    throw Fail{SDX_EINVAL};
+                                }
+                        } else {
+                            // the viscosity most children have; ties to the larger viscosity, then the smaller id
+                            int best = -1;
+                            for (int q = 0; q < 8; ++q) {
+                                int cnt = 0;
+                                for (int r = 0; r < 8; ++r) cnt += H->mu_table[kid[r]] == H->mu_table[kid[q]];
+                                const double mq = H->mu_table[kid[q]], mb = H->mu_table[id];
+                                if (cnt > best || (cnt == best && (mq > mb || (mq == mb && kid[q] < id)))) {
+                                    best = cnt;
+                                    id = kid[q];
+                                }
                             }
                         }
-                        cc[i + (size_t)mc * (j + (size_t)mc * k)] = id0;
+                        cc[i + (size_t)mc * (j + (size_t)mc * k)] = id;
                     }
             cells.swap(cc);
             m = mc;
@@ -398,6 +506,7 @@ Hier* hier_create(const sdx_desc* d) {
         H->use_coop = !(nc && nc[0] == '1');
         if (const char* cm = std::getenv("SDX_COOP_MAX_NODES")) H->coop_max_nodes = std::atoll(cm);
         if (const char* cm = std::getenv("SDX_CLUSTER_MAX_NODES")) H->cluster_max_nodes = std::atoll(cm);
+        if (const char* cm = std::getenv("SDX_CLUSTER_MAX_NODES_FP64")) H->cluster_max_nodes64 = std::atoll(cm);
         if (const char* cm = std::getenv("SDX_TEST_BARRIER_EXTRA")) H->coop_barrier_extra = (unsigned)std::atoi(cm);
         H->coop_bar = dalloc<unsigned>(2);
         H->coop_err = dalloc<int>(1);
@@ -581,6 +690,11 @@ static int solve(Hier& H, const double* b, double* x, double rtol, int maxit, in
         S.res = res;
         S.status = c;
         if (st) *st = S;
+        if (c == SDX_ENOCONV)
+            set_error("no convergence within maxit = " + std::to_string(maxit) + ": relative residual " +
+                      std::to_string(S.bnorm > 0 ? res / S.bnorm : res));
+        else if (c == SDX_ENONFINITE)
+            set_error("non-finite residual norm");
         return c;
     };
     if (!std::isfinite(res) || !std::isfinite(S.bnorm)) return finish(SDX_ENONFINITE);

@@ -30,6 +30,7 @@ constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle 
 // on levels of at most CLUSTER_MAX_NODES nodes.
 constexpr long long COOP_MAX_NODES = 0;
 constexpr long long CLUSTER_MAX_NODES = 10000;
+constexpr long long CLUSTER_MAX_NODES64 = 0;
 
 // Read-only view of one level as seen by kernels, for arithmetic type T.
 template <typename T>
@@ -48,6 +49,35 @@ struct LevelView {
     const T* idA;           // 1 / diag(A) of a uniform node: 1/(6 mu h), strain form 1/(8 mu h)
     const T* tauh;          // tau h [256]
     const T* idC;           // omega / diag(C) of a uniform node: omega / (6 tau h)
+    // Folded constants of the uniform-node updates (per id): the velocity update of row j is
+    // idA f_j + a1 A_j(p) + a2 A_pair(j)(p) + a3 D(p) plus the neighbour sum (stencil.cuh), the
+    // pressure update uses k12 = idC h^2 / 12.
+    const T* a1;            // idA h^2 / 3
+    const T* a2;            // -idA h^2 / 6
+    const T* a3;            // idA h^2 / 12
+    const T* k12;           // idC h^2 / 12
+    T h2_3, h2_6, h2_12;    // h^2 / 3, h^2 / 6, h^2 / 12 (the B stencils of the apply)
+};
+
+// Per-id table of a level: NTAB rows of 256 values, in the order of the LevelView pointers
+// muh, idA, tauh, idC, a1, a2, a3, k12.
+constexpr int NTAB = 8;
+
+// Coefficients of one special-row configuration (SpecRows::cfg indexes a table of these):
+// row component r (0..2 velocity, 3 pressure) times column (component c, Kuhn offset d) at
+// r * 60 + c * 15 + d, then diag(A) of the three velocity rows at 240..242 and diag(C) at 243.
+// A row's coefficients depend only on the eight cells around its node (viscosity ids, with the
+// ghost id outside the domain), on its interface flag and on the level, so nodes sharing these
+// share one configuration.
+constexpr int CFG_STRIDE = 244;
+constexpr int CFG_DIAG_A = 240;
+constexpr int CFG_DIAG_C = 243;
+
+// A list of special rows: node indices and their configuration indices.
+struct SpecRows {
+    int* node = nullptr;
+    int* cfg = nullptr;
+    int n = 0;
 };
 
 // Device buffers of one level.
@@ -62,20 +92,18 @@ struct Level {
     uint16_t* info = nullptr;
     double* tau_d = nullptr;
     float* tau_f = nullptr;
-    double* tab_d = nullptr;   // [4][256]: mu h, 1/diag(A), tau h, omega/diag(C)
+    double* tab_d = nullptr;   // [NTAB][256] per-id constants (see LevelView)
     float* tab_f = nullptr;
-    // special node lists (int32 node indices)
-    int* spec_all = nullptr;  int n_spec_all = 0;
-    int* spec_full = nullptr; int n_spec_full = 0;   // special rows with a free velocity component
-    int* spec_prow = nullptr; int n_spec_prow = 0;   // special rows with all velocity fixed
-    // precomputed stencil coefficients of the special rows (SoA: [coefficient][row]);
-    // column (component c, Kuhn offset d) has index c * 15 + d, row component r adds r * 60
-    double* cf_full_d = nullptr; float* cf_full_f = nullptr;      // 240 per row
-    double* cf_prow_d = nullptr; float* cf_prow_f = nullptr;      // 60 per row (pressure row)
-    double* cf_vel_d[2] = {nullptr, nullptr}; float* cf_vel_f[2] = {nullptr, nullptr};  // 180 + 3 diag
-    double* cf_pre_d[2] = {nullptr, nullptr}; float* cf_pre_f[2] = {nullptr, nullptr};  // 60 + 1 diag
-    int* spec_vel[2] = {nullptr, nullptr};  int n_spec_vel[2] = {0, 0};
-    int* spec_pre[2] = {nullptr, nullptr};  int n_spec_pre[2] = {0, 0};
+    // special rows (int32 node indices with their configuration indices)
+    SpecRows full;     // special rows with a free velocity component
+    SpecRows prow;     // special rows with all velocity fixed (pressure row only)
+    SpecRows vel[2];   // velocity rows of each colour (nodes with a free velocity component)
+    SpecRows pre[2];   // pressure rows of each colour (every special node)
+    // configuration table [n_cfg][CFG_STRIDE] (FP64, and an FP32 copy for FP32 cycles)
+    int n_cfg = 0;
+    int* cfg_rep = nullptr;    // a representative node of each configuration (device)
+    double* cft_d = nullptr;
+    float* cft_f = nullptr;
     long long free_dofs = 0;
     // work vectors (4 components unless noted)
     double* x = nullptr;  double* b = nullptr;  double* r = nullptr;
@@ -100,7 +128,8 @@ struct CycleGraph {
 
 struct Hier {
     int n = 0, n_coarse = 0, prec = 0;
-    int form = 0, coarse_form = 0;
+    int form = 0, coarse_form = 0, coarsest_form = 0;
+    bool coarse_correction = false;  // Sec. 5 right-hand-side correction of the coarsest solve
     double beta = 1.0 / 12.0;
     int face[6] = {0, 0, 0, 0, 0, 0};
     bool nullspace = false;
@@ -124,7 +153,8 @@ struct Hier {
     bool released = false;          // work vectors handed back (instance of a batch)
     bool use_coop = true;           // cooperative smoothing launches on small levels
     long long coop_max_nodes = COOP_MAX_NODES;
-    long long cluster_max_nodes = CLUSTER_MAX_NODES;
+    long long cluster_max_nodes = CLUSTER_MAX_NODES;      // FP32 levels
+    long long cluster_max_nodes64 = CLUSTER_MAX_NODES64;  // FP64 levels
     unsigned* coop_bar = nullptr;   // grid barrier state of the cooperative smoother [2]
     int* coop_err = nullptr;        // set when a barrier wait of that smoother timed out
     unsigned coop_barrier_extra = 0;  // test hook: barrier arrivals that never come (> 0 forces time-outs)
@@ -150,7 +180,8 @@ template <typename T>
 void launch_prolong_add(const Hier& H, int l, const T* ec, T* xf, cudaStream_t s);
 void launch_rhs(const Hier& H, const double* f, double* b, cudaStream_t s);
 
-// Build the special-row coefficient arrays of level l (FP64, and FP32 copies if allocated).
+// Build the configuration table of level l's special rows (FP64, and the FP32 copy if
+// allocated).
 void build_special_coefs(const Hier& H, int l, cudaStream_t s);
 
 // vector helpers over count elements
@@ -175,6 +206,10 @@ void launch_coarse_solve(const Hier& H, const T* b, T* x, cudaStream_t s);
 
 // Gauss-Jordan inverse with partial pivoting on the device; returns false if singular
 bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s);
+// kinv[:, nu + c] += sum_k kinv[:, rows[k]] vals[k] over colptr[c] <= k < colptr[c + 1], for the
+// nf - nu pressure columns c (kinv row-major nf x nf): kinv (I + E) with E stored by column
+void fold_coarse_correction(double* kinv, int nf, int nu, const int* colptr, const int* rows,
+                            const double* vals, cudaStream_t s);
 
 // Allocation-free velocity colour pass (decoupled and gradient forms, FP64): the special-row
 // scratch is a static device array of NOALLOC_MAX_ROWS rows.  Returns 0, -1 (bad argument,
@@ -182,6 +217,37 @@ bool device_inverse(double* a_dev, int n, double* inv_dev, cudaStream_t s);
 constexpr int NOALLOC_MAX_ROWS = 65536;
 int launch_velocity_pass_noalloc(const Hier& H, int l, int colour, double* x, const double* b,
                                  cudaStream_t s, std::string& err);
+
+// ---------------------------------------------------------------- launches
+// Kernels of the V-cycle and the solver are launched with programmatic dependent launch: a
+// kernel may be scheduled while the one before it on the stream still runs, and every such
+// kernel begins with pdl_prologue(), which waits until that predecessor has completed and its
+// writes are visible (griddepcontrol.wait) and then lets the next kernel be scheduled
+// (griddepcontrol.launch_dependents).  The launch latency of the many small kernels of the
+// coarse levels then overlaps the kernel before them.  SDX_NO_PDL=1 in the environment turns it
+// off (plain stream order).
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_prologue() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+#endif
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
 
 // kernel-launch counter (add the number of launches issued)
 void count_launches(long long k);

@@ -51,7 +51,9 @@ class sdx_desc(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int), ("n_coarse", ctypes.c_int),
                 ("cell_id", ctypes.POINTER(ctypes.c_uint8)), ("mu", ctypes.POINTER(ctypes.c_double)),
                 ("n_mu", ctypes.c_int), ("face", ctypes.c_int * 6), ("form", ctypes.c_int),
-                ("coarse_form", ctypes.c_int), ("prec", ctypes.c_int), ("pspg_beta", ctypes.c_double)]
+                ("coarse_form", ctypes.c_int), ("prec", ctypes.c_int), ("pspg_beta", ctypes.c_double),
+                ("coarsest_form", ctypes.c_int), ("coarse_correction", ctypes.c_int),
+                ("coarsening", ctypes.c_int)]
 
 
 class sdx_stats(ctypes.Structure):
@@ -179,7 +181,17 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta):
+def _form(f):
+    if f is None:
+        return -1
+    return FORMS[f] if isinstance(f, str) else int(f)
+
+
+COARSENING = {"resolved": 0, "majority": 1}
+
+
+def _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta, coarsest_form=None,
+               coarse_correction=False, coarsening="resolved"):
     """An sdx_desc for the arguments, plus the host arrays it points into (keep them alive)."""
     cell = np.ascontiguousarray(np.asarray(cell_id, dtype=np.uint8).ravel())
     mu_a = np.ascontiguousarray(np.asarray(mu, dtype=np.float64))
@@ -197,6 +209,9 @@ def _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta):
         d.coarse_form = FORMS[coarse_form] if isinstance(coarse_form, str) else int(coarse_form)
     d.prec = int(prec)
     d.pspg_beta = float(beta)
+    d.coarsest_form = _form(coarsest_form)
+    d.coarse_correction = 1 if coarse_correction else 0
+    d.coarsening = COARSENING[coarsening] if isinstance(coarsening, str) else int(coarsening)
     return d, (cell, mu_a)
 
 
@@ -205,9 +220,11 @@ class Hierarchy:
 
     def __init__(self, n: int, n_coarse: int, cell_id: np.ndarray, mu: Sequence[float],
                  face: Sequence[int], form="tr", coarse_form=None, prec=PREC_FP64,
-                 beta: float = 1.0 / 12.0):
+                 beta: float = 1.0 / 12.0, coarsest_form=None, coarse_correction: bool = False,
+                 coarsening="resolved"):
         lib = load()
-        d, self._keep = _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta)
+        d, self._keep = _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta,
+                                   coarsest_form, coarse_correction, coarsening)
         h = ctypes.c_void_p()
         _check(lib.sdx_create(ctypes.byref(d), ctypes.byref(h)))
         self._h = h
@@ -215,9 +232,17 @@ class Hierarchy:
         self.nn = (self.n + 1) ** 3
 
     @classmethod
-    def from_problem(cls, problem, form="tr", coarse_form=None, prec=PREC_FP64, beta=1.0 / 12.0):
+    def from_problem(cls, problem, form="tr", coarse_form=None, prec=PREC_FP64, beta=1.0 / 12.0,
+                     coarsest_form=None, coarse_correction=False, coarsening="resolved"):
         return cls(problem.n, problem.n_coarse, problem.cell_id, problem.mu, problem.face, form,
-                   coarse_form, prec, beta)
+                   coarse_form, prec, beta, coarsest_form, coarse_correction, coarsening)
+
+    @classmethod
+    def paper_coarse_variant(cls, problem, prec=PREC_FP64, beta=1.0 / 12.0):
+        """The coarse-grid variant of Sec. 5: decoupled form a_tr on every level but the
+        coarsest, which takes a_sym with the corrected momentum right-hand side."""
+        return cls.from_problem(problem, form="tr", coarse_form="tr", prec=prec, beta=beta,
+                                coarsest_form="sym", coarse_correction=True)
 
     def close(self):
         if getattr(self, "_borrowed", False):
@@ -357,12 +382,13 @@ class Batch:
     """Independent problems solved together by sdx_batch_* (owned; freed by close())."""
 
     def __init__(self, problems, form="tr", coarse_form=None, prec=PREC_FP32_REFINED,
-                 beta: float = 1.0 / 12.0, autotune: bool = True):
+                 beta: float = 1.0 / 12.0, autotune: bool = True, coarsening="resolved"):
         lib = load()
         descs = (sdx_desc * len(problems))()
         self._keep = []
         for i, p in enumerate(problems):
-            d, keep = _make_desc(p.n, p.n_coarse, p.cell_id, p.mu, p.face, form, coarse_form, prec, beta)
+            d, keep = _make_desc(p.n, p.n_coarse, p.cell_id, p.mu, p.face, form, coarse_form, prec, beta,
+                                 coarsening=coarsening)
             descs[i] = d
             self._keep.append(keep)
         h = ctypes.c_void_p()

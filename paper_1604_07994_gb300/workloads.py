@@ -275,6 +275,28 @@ def viscosity_layers(n: int, n_coarse: int = 4) -> Problem:
                    forcing=base.forcing, name=f"layers_{n}")
 
 
+def level_set_cell_ids(n: int, phi: Callable) -> np.ndarray:
+    """Cell ids of a level-set interface that the grid does not resolve: 1 where the level-set
+    function phi(x, y, z) is negative at the cell centre, else 0 ([n, n, n], [k, j, i])."""
+    c = (np.arange(n, dtype=np.float64) + 0.5) / n
+    z, y, x = np.meshgrid(c, c, c, indexing="ij")
+    return (np.asarray(phi(x, y, z)) < 0.0).astype(np.uint8)
+
+
+def level_set_sphere(n: int = 32, n_coarse: int = 4, seed: int = 6, mu_in: float = 1e3,
+                     mu_out: float = 1.0) -> Problem:
+    """A stiff sphere whose surface cuts the cells (phi = |x - c| - r, c and r seeded, the
+    sphere inside the cube): not aligned with any grid plane, so the coarser grids do not
+    resolve it.  No-slip walls, Gaussian-blob forcing."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    centre = rng.uniform(0.4, 0.6, 3)
+    radius = rng.uniform(0.17, 0.27)
+    ids = level_set_cell_ids(n, lambda x, y, z: np.sqrt((x - centre[0]) ** 2 + (y - centre[1]) ** 2
+                                                         + (z - centre[2]) ** 2) - radius)
+    return Problem(n=n, n_coarse=n_coarse, cell_id=ids, mu=np.array([mu_out, mu_in]),
+                   face=(DIRICHLET,) * 6, forcing=gaussian_blobs(seed), name=f"sphere_{n}")
+
+
 def random_vector(n: int, seed: int, dtype=np.float64) -> np.ndarray:
     """A seeded random SoA vector [4, (n+1)^3] (u_x, u_y, u_z, p), entries ~ U[-1, 1]."""
     rng = np.random.Generator(np.random.PCG64(seed))

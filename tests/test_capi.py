@@ -76,6 +76,17 @@ def test_strerror_and_argument_validation_without_a_device():
     cells8[5] = 3
     assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
     assert b"cell id" in lib.sdx_last_error()
+    cells8[5] = 0
+    # the Sec. 5 coarse-grid correction needs a coarser level with the strain form
+    d.coarsest_form, d.coarse_correction = sdx.FORM_DECOUPLED, 1
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert b"coarse_correction" in lib.sdx_last_error()
+    d.coarsest_form, d.n_coarse = sdx.FORM_STRAIN, 8  # a single level
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert b"coarse_correction" in lib.sdx_last_error()
+    d.coarse_correction, d.coarsest_form = 2, -1
+    assert lib.sdx_create(ctypes.byref(d), ctypes.byref(h)) == sdx.EINVAL
+    assert h.value is None
     # null hierarchy handles
     assert lib.sdx_apply(None, 0, None, None, None) == sdx.EINVAL
     assert lib.sdx_destroy(None) == sdx.OK
