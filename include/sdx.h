@@ -176,10 +176,11 @@ int sdx_smooth_pass_f32(sdx_hier_t h, int level, int which, int colour, const fl
                         void* stream);
 
 /* `steps` FP32 Uzawa smoothing steps (as sdx_uzawa, 1 <= steps <= 1000) on one level, in place
- * on the FP32 vector x, with exactly the launches the FP32 V-cycle uses on that level: on levels
- * of at most 10000 nodes all steps run in one thread-block cluster (hardware cluster barriers
- * between the colour passes), elsewhere one launch per pass.  Needs a hierarchy created with
- * prec = SDX_PREC_FP32_REFINED.  Paper: Sec. 5, eq. (Uzawa_smooth). */
+ * on the FP32 vector x, with exactly the launches the FP32 V-cycle uses on that level: one
+ * launch per pass, or, on levels of at most SDX_CLUSTER_MAX_NODES nodes (environment variable
+ * read when the hierarchy is created; default 0 = never), all steps in one thread-block
+ * cluster with hardware cluster barriers between the colour passes.  Needs a hierarchy created
+ * with prec = SDX_PREC_FP32_REFINED.  Paper: Sec. 5, eq. (Uzawa_smooth). */
 int sdx_uzawa_f32(sdx_hier_t h, int level, const float* b, float* x, int steps, void* stream);
 
 /* Allocation-free variant of the velocity pass of sdx_smooth_pass (which = 0), FP64.
@@ -226,10 +227,10 @@ int sdx_vcycle(sdx_hier_t h, const double* b, double* x, void* stream);
  * residual norm was NaN/Inf (x is then the last finite iterate or garbage, stats filled),
  * SDX_ETIMEOUT if a fused smoothing launch gave up a grid barrier after its bounded wait
  * (reported at the next synchronisation; x is then not meaningful).
- * The smoothing steps of small levels may run fused in one launch (one thread-block cluster
- * for FP32 levels of at most 10000 nodes; a cooperative grid launch when the environment
- * variable SDX_COOP_MAX_NODES is set to a node limit when the hierarchy is created; none when
- * SDX_NO_COOP=1); every variant gives the same bits as the per-pass launches. */
+ * The smoothing steps of small levels may run fused in one launch when the environment sets a
+ * node limit at hierarchy creation (SDX_CLUSTER_MAX_NODES / SDX_CLUSTER_MAX_NODES_FP64: one
+ * thread-block cluster; SDX_COOP_MAX_NODES: a cooperative grid launch; SDX_NO_COOP=1 disables
+ * both); by default every level uses one launch per pass.  Every variant gives the same bits. */
 int sdx_solve(sdx_hier_t h, const double* b, double* x, double rtol, int maxit, int outer,
               int restart, sdx_stats* stats, void* stream);
 

@@ -24,12 +24,16 @@ constexpr uint8_t CELL_OUTSIDE = 255;  // id of the ghost cells around the domai
 
 constexpr double OMEGA = 0.3;  // pressure Gauss-Seidel relaxation (Sec. 5)
 constexpr int COARSE_MAX_DOFS = 12000;  // dense inverse of the coarsest saddle matrix (1.2 GB)
-// Default size limits of the fused smoothing launches.  Grid-wide cooperative smoothing is off by
-// default: inside the captured V-cycle a grid barrier (about 10 us across the two dies) costs
-// more than the kernel boundary it replaces.  Single-cluster smoothing is used for FP32 cycles
-// on levels of at most CLUSTER_MAX_NODES nodes.
+// Default size limits of the fused smoothing launches (0 = off; the environment variables
+// SDX_COOP_MAX_NODES, SDX_CLUSTER_MAX_NODES and SDX_CLUSTER_MAX_NODES_FP64 set them when a
+// hierarchy is created).  Measured on GB300 inside the captured V-cycle: a grid barrier costs
+// about 10 us across the two dies, more than the kernel boundary it replaces; one
+// thread-block cluster (16 SMs) spends about 3.5 us per phase on its L2 round trips, more than
+// the per-pass launches, whose launch latency overlaps the kernel before them (programmatic
+// dependent launch): 0.57 vs 0.70 ms for the 16^3 level of an FP32 cycle, and 0.83 vs 2.45 ms
+// in FP64, where 16 SMs also lack the FP64 rate.
 constexpr long long COOP_MAX_NODES = 0;
-constexpr long long CLUSTER_MAX_NODES = 10000;
+constexpr long long CLUSTER_MAX_NODES = 0;
 constexpr long long CLUSTER_MAX_NODES64 = 0;
 
 // Read-only view of one level as seen by kernels, for arithmetic type T.

@@ -202,11 +202,17 @@ def test_fp32_single_pass_within_rounding_bound(sdx, name, form):
     ("cube16", "tr", None, 0), ("cube16", "sym", None, 0), ("boxes16", "tr", None, 0),
     ("layer16", "tr", "sym", 0), ("layer16", "tr", "sym", 1), ("columns16", "grad", None, 0),
     ("mixed48", "tr", "sym", 1), ("mixed48", "tr", "sym", 2), ("mixed48", "tr", None, 2)])
-def test_fp32_uzawa_steps_match_oracle(sdx, name, form, coarse_form, level, steps):
-    """`steps` FP32 Uzawa steps through the launches of the FP32 V-cycle: levels of at most
-    10000 nodes run all steps in one thread-block cluster (one launch, checked with the launch
-    counter), larger ones one launch per pass.  Against the oracle's FP64 steps at 1e-5."""
+@pytest.mark.parametrize("cluster", [False, True])
+def test_fp32_uzawa_steps_match_oracle(sdx, name, form, coarse_form, level, steps, cluster, monkeypatch):
+    """`steps` FP32 Uzawa steps through the launches of the FP32 V-cycle: one launch per pass,
+    or (cluster=True: SDX_CLUSTER_MAX_NODES=10000 when the hierarchy is created) all steps of a
+    level of at most 10000 nodes in one thread-block cluster (one launch, checked with the
+    launch counter).  Against the oracle's FP64 steps at 1e-5."""
     p, L = _oracle_level(name, form, level, coarse_form)
+    for k in ("SDX_NO_COOP", "SDX_COOP_MAX_NODES", "SDX_CLUSTER_MAX_NODES"):
+        monkeypatch.delenv(k, raising=False)
+    if cluster:
+        monkeypatch.setenv("SDX_CLUSTER_MAX_NODES", "10000")
     H = sdx.Hierarchy.from_problem(p, form=form, coarse_form=coarse_form, prec=1)
     x, b = _state(L, 80 + level, np.float32)
     xd, bd = _dev(x, torch.float32), _dev(b, torch.float32)
@@ -218,7 +224,7 @@ def test_fp32_uzawa_steps_match_oracle(sdx, name, form, coarse_form, level, step
         L.uzawa(x, b)
     err = _relmax(_host(xd), x)
     assert err <= STEPS_TOL, (name, form, level, steps, err)
-    if L.nn <= 10000:
+    if cluster and L.nn <= 10000:
         assert launches == 1  # the single-cluster path
     else:
         assert launches >= 5 * steps
