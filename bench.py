@@ -463,8 +463,8 @@ def run_layer(args, sdx, torch, W, stream):
 def run_batch(args, sdx, torch, count=None):
     """48 independent instances, sizes uniform in {32,48,64,96}^3, 1-4 boxes, contrast
     log-uniform in [1, 1e6], Gaussian-blob forcing; FP32 cycles in FP64 refinement, decoupled
-    form (a_sym on the coarse levels); one batch (persistent launches, graph-captured cycle,
-    autotuned block shapes) vs the same instances solved one after another."""
+    form (a_sym on the coarse levels); one batch (the persistent work-queue solver, and the
+    lock-step solver with one launch per phase) vs the same instances solved one after another."""
     from paper_1604_07994_gb300 import workloads as W
     count = count or args.batch_count
     probs = W.batched_instances(count)
@@ -480,22 +480,29 @@ def run_batch(args, sdx, torch, count=None):
         H.sdx_rhs(f, b)
         bs.append(b)
         xs.append(torch.zeros_like(b))
-    st = B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=400, restart=30)
-    torch.cuda.synchronize()
-    l0 = sdx.sdx_kernel_launches()
-    ts = []
-    for _ in range(3):
-        for x in xs:
-            x.zero_()
-        torch.cuda.synchronize()
-        t1 = time.perf_counter()
+    def timed(lockstep):
+        if lockstep:
+            os.environ["SDX_BATCH_LOCKSTEP"] = "1"
+        else:
+            os.environ.pop("SDX_BATCH_LOCKSTEP", None)
         st = B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=400, restart=30)
         torch.cuda.synchronize()
-        ts.append(time.perf_counter() - t1)
-    launches = (sdx.sdx_kernel_launches() - l0) / 3
+        l0 = sdx.sdx_kernel_launches()
+        ts = []
+        for _ in range(3):
+            for x in xs:
+                x.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            st = B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=400, restart=30)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t1)
+        os.environ.pop("SDX_BATCH_LOCKSTEP", None)
+        return min(ts), (sdx.sdx_kernel_launches() - l0) / 3, st
+    t_lock, launches_lock, st_lock = timed(True)
+    tb, launches, st = timed(False)
     its = [s["iterations"] for s in st]
     shapes = [B.sdx_batch_shape(lv) for lv in range(4)]
-    tb = min(ts)
     # the same instances, one hierarchy after another (same solver settings)
     tseq, its_seq = 0.0, []
     for p, b in zip(probs, bs):
@@ -515,8 +522,13 @@ def run_batch(args, sdx, torch, count=None):
             "total_free_dofs": int(free), "time_to_1e8_s": tb, "gdofs": free / tb / 1e9, "all_converged": all(s["status"] == 0 for s in st),
             "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)), "setup_s": setup,
             "gpu_launches_per_solve": int(launches), "block_shapes_per_level": shapes,
+            "solver": "one persistent launch over a device work queue: per-instance FGMRES(30) + V_var(3,3), no host synchronisation until the batch is done",
+            "lockstep_per_phase_launches": {"time_to_1e8_s": t_lock, "gdofs": free / t_lock / 1e9,
+                                            "gpu_launches_per_solve": int(launches_lock),
+                                            "iterations_max": int(max(s["iterations"] for s in st_lock))},
             "sequential_single_solves_s": tseq, "sequential_iterations_mean": float(np.mean(its_seq)),
-            "speedup_batched_vs_sequential": tseq / tb}
+            "sequential_gdofs": free / tseq / 1e9,
+            "speedup_batched_vs_sequential": tseq / tb, "speedup_queue_vs_lockstep": t_lock / tb}
 
 
 def vcycle_rate(torch, vcycle, residual, x, nn, w=None, cycles=40, last=10):
@@ -758,9 +770,38 @@ def run_conv(args, sdx, torch):
     t_f = _time(lambda: net.forward(n, x, y), 5, stream, torch)
     t_fb = _time(lambda: net.loss_grad(n, x, t), 5, stream, torch)
     pk = peaks().get("bf16_tflops")
+    # single convolutions of every shape at its level's size: brick kernel vs per-tap gather
+    single = {}
+    for ci, co, lv in sorted(set(layers)):
+        m = n >> lv
+        xs = torch.from_numpy(rng.standard_normal((m ** 3, ci)).astype(np.float32)).cuda().to(torch.bfloat16)
+        ws = torch.from_numpy((rng.standard_normal((27, co, ci)) / np.sqrt(27 * ci)).astype(np.float32)).cuda().to(torch.bfloat16)
+        ys = torch.empty((m ** 3, co), dtype=torch.float32, device="cuda")
+        fl = 2.0 * m ** 3 * 27 * ci * co
+        row = {}
+        for tag, env in (("brick", None), ("gather", "1")):
+            if env:
+                os.environ["SDX_CONV_GATHER"] = env
+            else:
+                os.environ.pop("SDX_CONV_GATHER", None)
+            tt = _time(lambda: sdx.sdx_conv3(m, ci, co, xs, ws, None, 0, ys), 10, stream, torch)
+            row[tag] = {"ms": tt, "tflops": fl / (tt * 1e-3) / 1e12}
+        os.environ.pop("SDX_CONV_GATHER", None)
+        dz = torch.from_numpy(rng.standard_normal((m ** 3, co)).astype(np.float32)).cuda().to(torch.bfloat16)
+        dw = torch.zeros((27, co, ci), dtype=torch.float32, device="cuda")
+        tw = _time(lambda: sdx.sdx_conv3_wgrad(m, ci, co, xs, dz, dw), 10, stream, torch)
+        row["wgrad"] = {"ms": tw, "tflops": fl / (tw * 1e-3) / 1e12}
+        single[f"{ci}->{co} at {m}^3"] = row
+    # inference on the 128^3 evaluation grid (the learned guess's use)
+    t_inf = None
+    if n != 128:
+        V2 = 128 ** 3
+        x2 = torch.from_numpy(rng.standard_normal((V2, 16)).astype(np.float32)).cuda().to(torch.bfloat16)
+        y2 = torch.empty((V2, 16), dtype=torch.float32, device="cuda")
+        t_inf = _time(lambda: net.forward(128, x2, y2), 5, stream, torch)
     return {"n": n, "cells": V, "forward_ms": t_f, "forward_backward_ms": t_fb,
             "forward_tflops": fwd_flops / (t_f * 1e-3) / 1e12, "train_step_tflops": 3 * fwd_flops / (t_fb * 1e-3) / 1e12,
-            "bf16_peak_tflops_measured": pk}
+            "forward_128_ms": t_inf, "single_convolutions": single, "bf16_peak_tflops_measured": pk}
 
 
 def run_guess(args, sdx, torch):

@@ -56,27 +56,34 @@ __host__ __device__ __forceinline__ long long colour_slots(int n1) {
 // The uniform-node bodies load a node's whole neighbourhood first and test whether the node is
 // special only afterwards, so that the test (which waits for the info word) does not hold back
 // the other loads: one round trip to memory per node instead of two.  The loads are volatile so
-// that they are issued where they stand.  With NC they use the read-only path, valid when no
-// thread of the launch writes what another reads (one colour pass or apply per launch: the
-// colouring, x != y); the fused smoothing kernels, whose phases read what earlier phases of the
-// same launch wrote, use plain loads (NC = false), which their barriers' acquire makes see
-// those writes.
-template <bool NC>
+// that they are issued where they stand.  Load policy LP:
+//   LD_NC (1): the read-only path, valid when no thread of the launch writes what another reads
+//              (one colour pass or apply per launch: the colouring, x != y);
+//   LD_PLAIN (0): plain loads, for the fused smoothing kernels, whose phases read what earlier
+//              phases of the same launch wrote and whose barriers' acquire makes them see it;
+//   LD_CG (2): loads that bypass L1, for the persistent batch solver, whose CTAs read what other
+//              CTAs wrote earlier in the launch after acquiring it through a fence.
+constexpr int LD_PLAIN = 0;
+constexpr int LD_NC = 1;
+constexpr int LD_CG = 2;
+template <int LP>
 __device__ __forceinline__ float ldx(const float* p) {
     float v;
-    if (NC) asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    if (LP == LD_NC) asm volatile("ld.global.nc.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    else if (LP == LD_CG) asm volatile("ld.global.cg.f32 %0, [%1];" : "=f"(v) : "l"(p));
     else asm volatile("ld.global.f32 %0, [%1];" : "=f"(v) : "l"(p));
     return v;
 }
-template <bool NC>
+template <int LP>
 __device__ __forceinline__ double ldx(const double* p) {
     double v;
-    if (NC) asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    if (LP == LD_NC) asm volatile("ld.global.nc.f64 %0, [%1];" : "=d"(v) : "l"(p));
+    else if (LP == LD_CG) asm volatile("ld.global.cg.f64 %0, [%1];" : "=d"(v) : "l"(p));
     else asm volatile("ld.global.f64 %0, [%1];" : "=d"(v) : "l"(p));
     return v;
 }
 template <typename T>
-__device__ __forceinline__ T ldro(const T* p) { return ldx<true>(p); }
+__device__ __forceinline__ T ldro(const T* p) { return ldx<LD_NC>(p); }
 __device__ __forceinline__ unsigned ldro_u16(const uint16_t* p) {
     unsigned v;
     asm volatile("ld.global.nc.u16 %0, [%1];" : "=r"(v) : "l"(p));
@@ -96,12 +103,12 @@ __device__ __forceinline__ void kuhn_offsets(const LevelView<T>& L, long long of
 }
 
 // The 14 neighbours v(b - d), v(b + d) of node b (no centre).
-template <bool NC, typename T>
+template <int LP, typename T>
 __device__ __forceinline__ void ld_nb14(const T* v, long long b, const long long off[7], T m[7], T p[7]) {
 #pragma unroll
     for (int d = 0; d < 7; ++d) {
-        m[d] = ldx<NC>(v + b - off[d]);
-        p[d] = ldx<NC>(v + b + off[d]);
+        m[d] = ldx<LP>(v + b - off[d]);
+        p[d] = ldx<LP>(v + b + off[d]);
     }
 }
 
@@ -139,7 +146,7 @@ __device__ __forceinline__ T bt_diffs(const T pm[7], const T pp[7], T A[7]) {
 // ------------------------------------------------------------------ apply / residual
 // y = K x (b == nullptr) or y = b - K x at one non-special node (a_tr / gradient form: the
 // velocity block is the mu-weighted 7-point Laplacian; strain form: stencil.cuh's a_sym rows).
-template <typename T, int FORM>
+template <typename T, int FORM, int LP = LD_NC>
 __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long long node,
                                                    const T* __restrict__ x, T* __restrict__ y,
                                                    const T* __restrict__ b) {
@@ -152,17 +159,17 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
     const unsigned inf = ldro_u16(L.info + node);
     const int id = (int)ldro_u8(L.cid + i + (long long)L.P * (j + (long long)L.P * k));
     T pm[7], pp[7], um[3][7], up[3][7], uc[3];
-    const T pc = ldro(x + 3 * nn + node);
-    ld_nb14<true>(x + 3 * nn, node, off, pm, pp);
+    const T pc = ldx<LP>(x + 3 * nn + node);
+    ld_nb14<LP>(x + 3 * nn, node, off, pm, pp);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        uc[c] = ldro(x + c * nn + node);
-        ld_nb14<true>(x + c * nn, node, off, um[c], up[c]);
+        uc[c] = ldx<LP>(x + c * nn + node);
+        ld_nb14<LP>(x + c * nn, node, off, um[c], up[c]);
     }
     T bv[4] = {0, 0, 0, 0};
     if (b)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) bv[c] = ldro(b + c * nn + node);
+        for (int c = 0; c < 4; ++c) bv[c] = ldx<LP>(b + c * nn + node);
     if (inf & INFO_SPECIAL) return;
     const T muh = L.muh[id];
     const T tauh = L.tauh[id];
@@ -210,7 +217,7 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
 // u_j: u_j = S_j / 6 + (f_j - (B^T p)_j) / (6 mu h); these rows read only velocities of the other
 // colour, in place.  The strain form (diag 8 mu h) reads same-colour velocities through its
 // cross-couplings and writes the new values into `out` (3 components).
-template <typename T, int FORM, bool NC = true>
+template <typename T, int FORM, int LP = LD_NC>
 __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, int j, int k,
                                                  T* __restrict__ x, const T* __restrict__ f,
                                                  T* __restrict__ out) {
@@ -222,15 +229,15 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
     const unsigned inf = ldro_u16(L.info + node);
     const int id = (int)ldro_u8(L.cid + i + (long long)L.P * (j + (long long)L.P * k));
     T pm[7], pp[7], fv[3];
-    ld_nb14<NC>(x + 3 * nn, node, off, pm, pp);
+    ld_nb14<LP>(x + 3 * nn, node, off, pm, pp);
     const int pair[3] = {EYZ, EXZ, EXY};
     if (FORM == FORM_SYM) {
         Nb15<T> U[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            U[c].c = ldx<NC>(x + c * nn + node);
-            ld_nb14<NC>(x + c * nn, node, off, U[c].m, U[c].p);
-            fv[c] = ldx<NC>(f + c * nn + node);
+            U[c].c = ldx<LP>(x + c * nn + node);
+            ld_nb14<LP>(x + c * nn, node, off, U[c].m, U[c].p);
+            fv[c] = ldx<LP>(f + c * nn + node);
         }
         if (inf & INFO_SPECIAL) return;
         const T idA = L.idA[id], a1 = L.a1[id], a2 = L.a2[id], a3 = L.a3[id];
@@ -250,10 +257,10 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             const T* u = x + c * nn + node;
-            um[c][0] = ldx<NC>(u - 1);    up[c][0] = ldx<NC>(u + 1);
-            um[c][1] = ldx<NC>(u - L.s1); up[c][1] = ldx<NC>(u + L.s1);
-            um[c][2] = ldx<NC>(u - L.s2); up[c][2] = ldx<NC>(u + L.s2);
-            fv[c] = ldx<NC>(f + c * nn + node);
+            um[c][0] = ldx<LP>(u - 1);    up[c][0] = ldx<LP>(u + 1);
+            um[c][1] = ldx<LP>(u - L.s1); up[c][1] = ldx<LP>(u + L.s1);
+            um[c][2] = ldx<LP>(u - L.s2); up[c][2] = ldx<LP>(u + L.s2);
+            fv[c] = ldx<LP>(f + c * nn + node);
         }
         if (inf & INFO_SPECIAL) return;
         const T idA = L.idA[id], a1 = L.a1[id], a2 = L.a2[id], a3 = L.a3[id];
@@ -268,19 +275,19 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
 }
 
 // Strain form: copy the colour's new value of one uniform node back from `src`.
-template <typename T>
+template <typename T, int LP = LD_PLAIN>
 __device__ __forceinline__ void vel_copy_node(const LevelView<T>& L, int i, int j, int k,
                                               const T* __restrict__ src, T* __restrict__ x) {
     const long long node = i + L.s1 * j + L.s2 * k;
     if (L.info[node] & INFO_SPECIAL) return;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) x[c * L.nn + node] = src[c * L.nn + node];
+    for (int c = 0; c < 3; ++c) x[c * L.nn + node] = ldx<LP>(src + c * L.nn + node);
 }
 
 // Pressure Gauss-Seidel on C p = B u - g with relaxation OMEGA at one non-special node:
 // p += omega (B u - tau h (6 p - S_p) - g) / (6 tau h), evaluated as
 // (1 - omega) p + (omega / 6) S_p + idC h^2 B u - idC g with idC = omega / (6 tau h).
-template <typename T, bool NC = true>
+template <typename T, int LP = LD_NC>
 __device__ __forceinline__ void pre_uniform_node(const LevelView<T>& L, int i, int j, int k,
                                                  T* __restrict__ x, const T* __restrict__ g) {
     if (!interior_node(L.n, i, j, k)) return;
@@ -292,12 +299,12 @@ __device__ __forceinline__ void pre_uniform_node(const LevelView<T>& L, int i, i
     const int id = (int)ldro_u8(L.cid + i + (long long)L.P * (j + (long long)L.P * k));
     T um[3][7], up[3][7];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) ld_nb14<NC>(x + c * nn, node, off, um[c], up[c]);
+    for (int c = 0; c < 3; ++c) ld_nb14<LP>(x + c * nn, node, off, um[c], up[c]);
     T* p = x + 3 * nn;
-    const T pc = ldx<NC>(p + node);
-    const T sp = ((ldx<NC>(p + node - 1) + ldx<NC>(p + node + 1)) + (ldx<NC>(p + node - L.s1) + ldx<NC>(p + node + L.s1))) +
-                 (ldx<NC>(p + node - L.s2) + ldx<NC>(p + node + L.s2));
-    const T gv = ldx<NC>(g + node);
+    const T pc = ldx<LP>(p + node);
+    const T sp = ((ldx<LP>(p + node - 1) + ldx<LP>(p + node + 1)) + (ldx<LP>(p + node - L.s1) + ldx<LP>(p + node + L.s1))) +
+                 (ldx<LP>(p + node - L.s2) + ldx<LP>(p + node + L.s2));
+    const T gv = ldx<LP>(g + node);
     if (inf & INFO_SPECIAL) return;
     T tsum, dsum;
     bu_sums(um, up, tsum, dsum);
@@ -315,7 +322,7 @@ __device__ __forceinline__ void pre_uniform_node(const LevelView<T>& L, int i, i
 // MODE 0: y = K x (or b - K x) on a full row; MODE 3: the same on a pressure-only row
 // (velocity rows written as 0); MODE 1: new velocity values of a colour into
 // y[3 * slot + r]; MODE 2: pressure Gauss-Seidel in place (b = g).
-template <typename T, int MODE>
+template <typename T, int MODE, int LP = LD_PLAIN>
 __device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* __restrict__ list,
                                               const int* __restrict__ cfgs,
                                               const T* __restrict__ cft, T* __restrict__ x,
@@ -339,7 +346,7 @@ __device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* 
     for (int d = 0; d < 15; ++d) {
         const int a = i + KOFF15[d][0], bb = j + KOFF15[d][1], cc = k + KOFF15[d][2];
         if (a < 0 || bb < 0 || cc < 0 || a >= L.n1 || bb >= L.n1 || cc >= L.n1) continue;
-        const T xv = xq[a + L.s1 * bb + L.s2 * cc];
+        const T xv = ldx<LP>(xq + a + L.s1 * bb + L.s2 * cc);
 #pragma unroll
         for (int r = 0; r < NR; ++r) acc[r] += cf[(R0 + r) * 60 + q * 15 + d] * xv;
     }
@@ -353,42 +360,42 @@ __device__ __forceinline__ void spec_row_quad(const LevelView<T>& L, const int* 
     if (MODE == 0) {
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
-            T out = b ? b[r * nn + node] - acc[r] : acc[r];
+            T out = b ? ldx<LP>(b + r * nn + node) - acc[r] : acc[r];
             if (r < 3 && (inf & (1u << r))) out = T(0);
             y[r * nn + node] = out;
         }
     } else if (MODE == 3) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) y[r * nn + node] = T(0);
-        y[3 * nn + node] = b ? b[3 * nn + node] - acc[0] : acc[0];
+        y[3 * nn + node] = b ? ldx<LP>(b + 3 * nn + node) - acc[0] : acc[0];
     } else if (MODE == 1) {
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
             T v = T(0);
             if (!(inf & (1u << r)))
-                v = x[r * nn + node] + (b[r * nn + node] - acc[r]) / cf[CFG_DIAG_A + r];
+                v = ldx<LP>(x + r * nn + node) + (ldx<LP>(b + r * nn + node) - acc[r]) / cf[CFG_DIAG_A + r];
             y[3 * (long long)slot + r] = v;
         }
     } else {
         T* p = x + 3 * nn;
-        p[node] = p[node] + T(OMEGA) * (acc[0] - b[node]) / cf[CFG_DIAG_C];
+        p[node] = ldx<LP>(p + node) + T(OMEGA) * (acc[0] - ldx<LP>(b + node)) / cf[CFG_DIAG_C];
     }
 }
 
 // Write the staged new velocity values of special row `slot` into x.
-template <typename T>
+template <typename T, int LP = LD_PLAIN>
 __device__ __forceinline__ void vel_scatter_slot(const int* __restrict__ list, int slot,
                                                  const T* __restrict__ tmp, T* __restrict__ x,
                                                  long long nn) {
     const long long node = list[slot];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) x[c * nn + node] = tmp[3 * (long long)slot + c];
+    for (int c = 0; c < 3; ++c) x[c * nn + node] = ldx<LP>(tmp + 3 * (long long)slot + c);
 }
 
 // ------------------------------------------------------------------ transfers
 // b_c = P^T r_f at coarse node `node`: r_f(2I) + 1/2 sum_d r_f(2I + d) over the 14 Kuhn edge
 // directions (fine midpoints of the coarse edges at I).
-template <typename T>
+template <typename T, int LP = LD_PLAIN>
 __device__ __forceinline__ void restrict_node(const LevelView<T>& F, const LevelView<T>& C,
                                               const T* __restrict__ rf, T* __restrict__ bc,
                                               long long node) {
@@ -405,16 +412,16 @@ __device__ __forceinline__ void restrict_node(const LevelView<T>& F, const Level
         for (int d = 0; d < 14; ++d) {
             const int a = fi + KUHN14[d][0], bb = fj + KUHN14[d][1], cc = fk + KUHN14[d][2];
             if (a < 0 || bb < 0 || cc < 0 || a >= F.n1 || bb >= F.n1 || cc >= F.n1) continue;
-            acc += r[a + F.s1 * bb + F.s2 * cc];
+            acc += ldx<LP>(r + a + F.s1 * bb + F.s2 * cc);
         }
-        T v = r[fb] + T(0.5) * acc;
+        T v = ldx<LP>(r + fb) + T(0.5) * acc;
         if (c < 3 && (inf & (1u << c))) v = T(0);
         bc[c * C.nn + node] = v;
     }
 }
 
 // x_f += P e_c at fine node `node` = (2I+a, 2J+b, 2K+c): the mean of e_c at I and I+(a,b,c).
-template <typename T>
+template <typename T, int LP = LD_PLAIN>
 __device__ __forceinline__ void prolong_node(const LevelView<T>& F, const LevelView<T>& C,
                                              const T* __restrict__ ec, T* __restrict__ xf,
                                              long long node) {
@@ -429,8 +436,8 @@ __device__ __forceinline__ void prolong_node(const LevelView<T>& F, const LevelV
     for (int c = 0; c < 4; ++c) {
         if (c < 3 && (inf & (1u << c))) continue;
         const T* e = ec + c * C.nn;
-        T v = mid ? T(0.5) * (e[c0] + e[c1]) : e[c0];
-        xf[c * F.nn + node] += v;
+        T v = mid ? T(0.5) * (ldx<LP>(e + c0) + ldx<LP>(e + c1)) : ldx<LP>(e + c0);
+        xf[c * F.nn + node] = ldx<LP>(xf + c * F.nn + node) + v;
     }
 }
 

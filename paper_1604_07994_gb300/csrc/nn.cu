@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <random>
 #include <string>
@@ -264,6 +265,130 @@ __global__ void __launch_bounds__(128) k_conv_fwd(ConvArgs a) {
     tc_fence_before();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, NCOL);
+}
+
+// ---------------------------------------------------------------- forward convolution, bricks
+// The same convolution with the input staged once per CTA.  A CTA owns an output brick of
+// BX x BY x ZB cells (x fastest).  Its input with a one-cell halo, (BX+2) x (BY+2) x (ZB+2) cells
+// (zero outside the grid), is stored in shared memory as CIN/8 planes of 16-byte cell rows in
+// x-fastest order, and all 27 taps' weights in the canonical K-major layout.  For output z-plane
+// zz the MMA's A operand (M = 128 = BX x BY cells, K = 16 channels) is then a view of the brick:
+// core matrix (group of 8 rows = one x-line of 8 cells, 16 bytes = 8 channels) at
+// start + y * (BX+2) * 16 (SBO) and + plane (LBO), and a tap (dx, dy, dz) only moves the start
+// address.  One elected thread issues 27 x ZB x CIN/16 MMAs into ZB accumulators in tensor
+// memory and one commit; there is no gather and no barrier per tap.
+constexpr int BR_X = 8, BR_Y = 16;
+
+template <int CIN, int COUT, int ZB>
+struct BrickShape {
+    static constexpr int HX = BR_X + 2, HY = BR_Y + 2, HZ = ZB + 2;
+    static constexpr int NQ = CIN / 8;
+    static constexpr int PLANE = HZ * HY * HX * 16;   // bytes of one 8-channel plane
+    static constexpr int BRICK = NQ * PLANE;
+    static constexpr int WTAP = COUT * CIN * 2;       // bytes of one tap's weights
+    static constexpr int SMEM = BRICK + 27 * WTAP;
+    static constexpr int NCOL = tmem_cols(ZB * COUT);
+};
+
+template <int CIN, int COUT, int ZB>
+__global__ void __launch_bounds__(128) k_conv_brick(ConvArgs a) {
+    using S = BrickShape<CIN, COUT, ZB>;
+    constexpr uint32_t IDESC = idesc_bf16(128, COUT);
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* sBrick = smem;
+    uint8_t* sW = smem + S::BRICK;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ uint32_t tslot;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    const int n = a.n;
+    const int x0 = blockIdx.x * BR_X, y0 = blockIdx.y * BR_Y, z0 = blockIdx.z * ZB;
+    if (warp == 0) tmem_alloc(smem_u32(&tslot), S::NCOL);
+    if (tid == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        mbar_init_fence();
+    }
+    // the brick with its halo: 16-byte chunk q fastest, then x, y, z (coalesced reads)
+    for (int idx = tid; idx < S::NQ * S::HX * S::HY * S::HZ; idx += 128) {
+        const int q = idx % S::NQ;
+        int r = idx / S::NQ;
+        const int hx = r % S::HX;
+        r /= S::HX;
+        const int hy = r % S::HY, hz = r / S::HY;
+        const int i = x0 + hx - 1, j = y0 + hy - 1, k = z0 + hz - 1;
+        uint4 val = make_uint4(0, 0, 0, 0);
+        if (i >= 0 && j >= 0 && k >= 0 && i < n && j < n && k < n)
+            val = *reinterpret_cast<const uint4*>(a.x + (i + (long long)n * (j + (long long)n * k)) * CIN + q * 8);
+        *reinterpret_cast<uint4*>(sBrick + q * S::PLANE + ((hz * S::HY + hy) * S::HX + hx) * 16) = val;
+    }
+    for (int idx = tid; idx < 27 * COUT * S::NQ; idx += 128) {
+        const int q = idx % S::NQ;
+        const int r = idx / S::NQ;
+        const int co = r % COUT, t = r / COUT;
+        const uint4 val = *reinterpret_cast<const uint4*>(a.w + ((long long)t * COUT + co) * CIN + q * 8);
+        *reinterpret_cast<uint4*>(sW + t * S::WTAP + kmajor_off(co, q * 8, CIN)) = val;
+    }
+    fence_async_smem();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    if (tid == 0) {
+        const uint32_t b0 = smem_u32(sBrick), w0 = smem_u32(sW);
+        for (int zz = 0; zz < ZB; ++zz) {
+            for (int t = 0; t < 27; ++t) {
+                int dx, dy, dz;
+                tap_offset(t, dx, dy, dz);
+                const uint32_t line = (uint32_t)(((zz + dz + 1) * S::HY + (dy + 1)) * S::HX + (dx + 1)) * 16;
+#pragma unroll
+                for (int s = 0; s < CIN / 16; ++s)
+                    mma_bf16(tmem + zz * COUT, sdesc(b0 + 2 * s * S::PLANE + line, S::PLANE, S::HX * 16),
+                             sdesc(w0 + t * S::WTAP + s * 256, 128, CIN * 16), IDESC, (t | s) != 0);
+            }
+        }
+        mma_commit(smem_u32(&bar));
+    }
+    bool ok = mbar_wait(smem_u32(&bar), 0, a.err);
+    ok = __syncthreads_and(ok);
+    if (!ok) mbar_wait(smem_u32(&bar), 0, nullptr);  // bounded: the one commit before freeing TMEM
+    tc_fence_after();
+    if (ok) {
+        const int m = warp * 32 + (tid & 31);
+        const int i = x0 + (m & 7), j = y0 + (m >> 3);
+        for (int zz = 0; zz < ZB; ++zz) {
+            const int k = z0 + zz;
+            const bool in = i < n && j < n && k < n;
+            const long long v = i + (long long)n * (j + (long long)n * k);
+#pragma unroll
+            for (int g = 0; g < COUT / 16; ++g) {
+                float acc[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + zz * COUT + g * 16, acc);
+                if (!in) continue;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    float val = acc[c];
+                    if (a.bias) val += a.bias[g * 16 + c];
+                    if (a.skip) val += __bfloat162float(a.skip[v * COUT + g * 16 + c]);
+                    if (a.relu) val = fmaxf(val, 0.0f);
+                    acc[c] = val;
+                }
+                if (a.yf) {
+                    float4* dst = reinterpret_cast<float4*>(a.yf + v * COUT + g * 16);
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) dst[c] = make_float4(acc[4 * c], acc[4 * c + 1], acc[4 * c + 2], acc[4 * c + 3]);
+                } else {
+                    __align__(16) bf16 o[16];
+#pragma unroll
+                    for (int c = 0; c < 16; ++c) o[c] = __float2bfloat16(acc[c]);
+                    uint4* dst = reinterpret_cast<uint4*>(a.ybf + v * COUT + g * 16);
+                    dst[0] = reinterpret_cast<const uint4*>(o)[0];
+                    dst[1] = reinterpret_cast<const uint4*>(o)[1];
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, S::NCOL);
 }
 
 // ---------------------------------------------------------------- weight gradient
@@ -641,10 +766,39 @@ __global__ void k_absmax(const double* __restrict__ f, long long count, double* 
 }
 
 // ---------------------------------------------------------------- launchers
+// Brick convolution of one shape: z-planes per brick chosen so that the brick, its halo and all
+// 27 taps' weights fit in shared memory (at most 203 KB, for 64 -> 32).
+template <int CIN, int COUT, int ZB>
+static void launch_brick(const ConvArgs& a, cudaStream_t s) {
+    using S = BrickShape<CIN, COUT, ZB>;
+    static bool attr = false;
+    if (!attr) {
+        CK(cudaFuncSetAttribute(k_conv_brick<CIN, COUT, ZB>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM));
+        attr = true;
+    }
+    const dim3 grid((a.n + BR_X - 1) / BR_X, (a.n + BR_Y - 1) / BR_Y, (a.n + ZB - 1) / ZB);
+    k_conv_brick<CIN, COUT, ZB><<<grid, 128, S::SMEM, s>>>(a);
+}
+
+// SDX_CONV_GATHER=1 selects the per-tap gather kernel (k_conv_fwd) instead of the brick kernel
+// (read at every launch, for comparisons).
+static bool use_gather_conv() {
+    const char* e = std::getenv("SDX_CONV_GATHER");
+    return e && e[0] == '1';
+}
+
 static void launch_conv(int cin, int cout, const ConvArgs& a, cudaStream_t s) {
     const long long V = (long long)a.n * a.n * a.n;
     const unsigned grid = (unsigned)((V + CONV_M - 1) / CONV_M);
     count_launches(1);
+    if (!use_gather_conv()) {
+        if (cin == 16 && cout == 16) { launch_brick<16, 16, 4>(a, s); return; }
+        if (cin == 16 && cout == 32) { launch_brick<16, 32, 4>(a, s); return; }
+        if (cin == 32 && cout == 16) { launch_brick<32, 16, 4>(a, s); return; }
+        if (cin == 32 && cout == 32) { launch_brick<32, 32, 4>(a, s); return; }
+        if (cin == 32 && cout == 64) { launch_brick<32, 64, 2>(a, s); return; }
+        if (cin == 64 && cout == 32) { launch_brick<64, 32, 2>(a, s); return; }
+    }
 #define SDX_CONV_CASE(I, O) \
     if (cin == I && cout == O) { k_conv_fwd<I, O><<<grid, 128, 0, s>>>(a); return; }
     SDX_CONV_CASE(16, 16) SDX_CONV_CASE(16, 32) SDX_CONV_CASE(32, 16) SDX_CONV_CASE(32, 32)

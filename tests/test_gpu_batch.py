@@ -1,5 +1,7 @@
 """GPU parity of the batched driver (sdx_batch_*): many independent problems of uneven sizes,
-depths, viscosity layouts and boundary faces advanced by one persistent launch per phase.
+depths, viscosity layouts and boundary faces.  sdx_batch_solve runs every instance's FGMRES in
+one persistent launch over a device work queue (default) or, with SDX_BATCH_LOCKSTEP=1, one
+launch per phase with the instances' Krylov steps in lock step; both are tested.
 
 * One batched V-cycle equals, instance by instance, the single-hierarchy sdx_vcycle (FP64:
   to 1e-14 relative, i.e. roundoff of the same arithmetic; FP32 cycles: 1e-5, since the
@@ -95,8 +97,19 @@ def test_batch_vcycle_matches_single_vcycles(sdx, form, coarse_form, prec):
             assert err <= (1e-14 if prec == 0 else 1e-5), (probs[k].name, err)
 
 
-@pytest.mark.parametrize("form,coarse_form,prec", [("tr", None, 0), ("tr", None, 1), ("tr", "sym", 1), ("sym", None, 1)])
-def test_batch_solve_matches_direct_solutions(sdx, form, coarse_form, prec):
+@pytest.fixture(params=["queue", "lockstep"])
+def solver(request, monkeypatch):
+    """The batch solver under test (read by sdx_batch_solve at every call)."""
+    if request.param == "lockstep":
+        monkeypatch.setenv("SDX_BATCH_LOCKSTEP", "1")
+    else:
+        monkeypatch.delenv("SDX_BATCH_LOCKSTEP", raising=False)
+    return request.param
+
+
+@pytest.mark.parametrize("form,coarse_form,prec", [("tr", None, 0), ("tr", None, 1), ("tr", "sym", 1), ("sym", None, 1),
+                                                   ("grad", "sym", 0)])
+def test_batch_solve_matches_direct_solutions(sdx, form, coarse_form, prec, solver):
     probs = _small_batch()
     B = sdx.Batch(probs, form=form, coarse_form=coarse_form, prec=prec)
     bs, xs, refs = [], [], []
@@ -120,7 +133,7 @@ def test_batch_solve_matches_direct_solutions(sdx, form, coarse_form, prec):
     assert len(its) > 1  # instances converged on their own schedules inside one batch
 
 
-def test_batch_edge_cases(sdx):
+def test_batch_edge_cases(sdx, solver):
     """A zero right-hand side converges at once (x stays 0) while the others iterate, and a
     one-instance batch gives the same bits as the same instance inside a larger batch."""
     probs = [W.cube_inclusion(8, 4), W.random_instance(12, 3, 9, 3, log10_contrast=(0, 4))]
@@ -147,7 +160,7 @@ def test_batch_edge_cases(sdx):
     assert e.value.code == sdx.EINVAL
 
 
-def test_batch_benchmark_sizes_reach_tolerance(sdx):
+def test_batch_benchmark_sizes_reach_tolerance(sdx, solver):
     """Instances of the benchmark family ({32,48,64,96}^3 cells, 1-4 boxes, contrast
     log-uniform in [1, 1e6], FP32 cycles in FP64 refinement): every instance's residual,
     recomputed in FP64 by the single-hierarchy sdx_residual, meets 1e-8."""
@@ -173,7 +186,7 @@ def test_batch_benchmark_sizes_reach_tolerance(sdx):
         H.close()
 
 
-def test_batch_statuses_are_per_instance(sdx):
+def test_batch_statuses_are_per_instance(sdx, solver):
     """A NaN in one instance's right-hand side marks that instance SDX_ENONFINITE (and the call
     returns it) while the other instance still converges in the same batch."""
     probs = [W.cube_inclusion(8, 4), W.random_instance(12, 3, 9, 3, log10_contrast=(0, 4))]
@@ -201,3 +214,24 @@ def test_destroy_refuses_a_batch_owned_hierarchy(sdx):
     st = B.sdx_batch_solve([_dev(b)], [x], rtol=1e-8, maxit=100)
     assert st[0]["res"] <= 1e-8 * st[0]["bnorm"]
     B.close()
+
+
+def test_queue_solver_is_deterministic_and_matches_lockstep_iterations(sdx, monkeypatch):
+    """The persistent solver gives the same bits on a repeated call (which CTA runs which tile
+    does not change any sum), and each instance needs the same number of FGMRES iterations as
+    in the lock-step solver (same preconditioner; the Gram-Schmidt arithmetic differs only in
+    rounding), give or take one."""
+    probs = _small_batch()
+    B = sdx.Batch(probs, form="tr", coarse_form="sym", prec=1)
+    bs = [_dev(_rhs(p)[0]) for p in probs]
+    runs = []
+    for env in ("0", "0", "1"):
+        monkeypatch.setenv("SDX_BATCH_LOCKSTEP", env)
+        xs = [torch.zeros_like(b) for b in bs]
+        st = B.sdx_batch_solve(bs, xs, rtol=1e-10, maxit=300, restart=30)
+        runs.append(([_host(x) for x in xs], [s["iterations"] for s in st]))
+    for a, b in zip(runs[0][0], runs[1][0]):
+        assert np.array_equal(a, b)
+    assert runs[0][1] == runs[1][1]
+    for iq, il in zip(runs[0][1], runs[2][1]):
+        assert abs(iq - il) <= 1

@@ -43,9 +43,10 @@ def _rng(seed):
 
 @pytest.mark.parametrize("relu", [0, 1])
 @pytest.mark.parametrize("cin,cout", SHAPES)
-def test_conv3_matches_oracle(sdx, cin, cout, relu):
-    n = 12  # 1728 cells: 13.5 tiles of 128, a ragged last tile
-    r = _rng(cin * 100 + cout + relu)
+@pytest.mark.parametrize("n", [12, 20])
+def test_conv3_matches_oracle(sdx, cin, cout, relu, n):
+    """n = 12 and 20: output bricks of 8 x 16 x ZB cells cut by the grid in x, y and z."""
+    r = _rng(cin * 100 + cout + relu + n)
     xd, x = _bf16(r.standard_normal((n ** 3, cin)))
     wd, w = _bf16(r.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
     b = r.standard_normal(cout).astype(np.float32)
@@ -56,6 +57,24 @@ def test_conv3_matches_oracle(sdx, cin, cout, relu):
         ref = np.maximum(ref, 0.0)
     got = y.cpu().numpy()
     assert np.abs(got - ref).max() <= 1e-3 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("gather", [0, 1])
+def test_conv3_full_bricks_and_gather_kernel(sdx, gather, monkeypatch):
+    """32^3 cells (whole bricks), 16 -> 16, FP32 output, through the brick kernel and through
+    the per-tap gather kernel (SDX_CONV_GATHER=1): both compute the oracle's convolution."""
+    if gather:
+        monkeypatch.setenv("SDX_CONV_GATHER", "1")
+    else:
+        monkeypatch.delenv("SDX_CONV_GATHER", raising=False)
+    n, cin, cout = 32, 16, 16
+    r = _rng(77)
+    xd, x = _bf16(r.standard_normal((n ** 3, cin)))
+    wd, w = _bf16(r.standard_normal((27, cout, cin)) / np.sqrt(27 * cin))
+    y = torch.empty((n ** 3, cout), dtype=torch.float32, device="cuda")
+    sdx.sdx_conv3(n, cin, cout, xd, wd, None, 0, y)
+    ref = ON.conv3(x, w, n, np.zeros(cout))
+    assert np.abs(y.cpu().numpy() - ref).max() <= 1e-3 * np.abs(ref).max()
 
 
 @pytest.mark.parametrize("cin,cout", SHAPES)
