@@ -74,6 +74,7 @@ struct QState {
     int vc_pos;                        // position in the V-cycle program
     int j, its, restarts, pass, status, first;
     double bnorm, res0, res, tol, scal;
+    long long t_done;                  // globaltimer (ns) when the instance finished
 };
 
 // Device-side view of one level for the kernel.
@@ -510,6 +511,9 @@ __device__ void handle(const QArgs& a, int i, QState& S, double* red, double* sh
     } else {
         S.status = code;
         S.kind = Q_DONE;
+        unsigned long long t;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+        a.st[i].t_done = (long long)t;
     }
     S.ntiles = tiles;
     S.seq = S.seq + 1;
@@ -531,7 +535,7 @@ __device__ void handle(const QArgs& a, int i, QState& S, double* red, double* sh
 template <typename T, int LP, int MINB>
 __global__ void __launch_bounds__(256, MINB) kq_solve(QArgs a) {
     __shared__ QState S;
-    __shared__ int s_inst, s_tile, s_quit, s_last;
+    __shared__ int s_inst, s_tile, s_cnt, s_quit, s_last, s_reload;
     __shared__ double sh[32];
     __shared__ double red[QMAX_M + 1];
     const int count = a.count;
@@ -540,6 +544,8 @@ __global__ void __launch_bounds__(256, MINB) kq_solve(QArgs a) {
     unsigned seen = 0;
     long long idle0 = 0;
     int backoff = 32;
+    int cached_inst = -1;        // instance and phase whose state S holds (thread 0)
+    unsigned cached_seq = 0;
     while (true) {
         if (threadIdx.x == 0) {
             s_inst = -1;
@@ -547,11 +553,20 @@ __global__ void __launch_bounds__(256, MINB) kq_solve(QArgs a) {
             for (int q = 0; q < count && s_inst < 0; ++q) {
                 const int ii = rr + q < count ? rr + q : rr + q - count;
                 const unsigned long long w0 = *(volatile unsigned long long*)(a.word + ii);
-                if (wclaimed(w0) >= wtiles(w0)) continue;
-                const unsigned long long w = atomicAdd(a.word + ii, 1ULL);
-                if (wclaimed(w) < wtiles(w)) {
+                const unsigned tiles0 = wtiles(w0);
+                if (wclaimed(w0) >= tiles0) continue;
+                // several tiles per claim when the phase is large (fewer atomics per tile)
+                const unsigned K = min(8u, max(1u, tiles0 / (4u * gridDim.x)));
+                const unsigned long long w = atomicAdd(a.word + ii, (unsigned long long)K);
+                const unsigned c = wclaimed(w), tiles = wtiles(w);
+                if (c < tiles) {
+                    const unsigned seq = (unsigned)(w >> 44);
                     s_inst = ii;
-                    s_tile = (int)wclaimed(w);
+                    s_tile = (int)c;
+                    s_cnt = (int)min(K, tiles - c);
+                    s_reload = !(ii == cached_inst && seq == cached_seq);
+                    cached_inst = ii;
+                    cached_seq = seq;
                 }
             }
             if (s_inst >= 0) {
@@ -580,16 +595,23 @@ __global__ void __launch_bounds__(256, MINB) kq_solve(QArgs a) {
         if (s_quit) break;
         const int inst = s_inst;
         if (inst >= 0) {
-            __threadfence();  // acquire: the phase's inputs were published before its word
-            if (threadIdx.x == 0) load_state(a.st + inst, S);
+            if (s_reload) {  // first tiles of this phase on this CTA
+                __threadfence();  // acquire: the phase's inputs were published before its word
+                if (threadIdx.x == 0) load_state(a.st + inst, S);
+                __syncthreads();
+            }
+            for (int t = 0; t < s_cnt; ++t) {
+                if (S.kind < Q_DOT_B) cycle_tile<T, LP>(a, inst, S.kind, S.level, S.colour, s_tile + t);
+                else krylov_tile<T, LP>(a, inst, S, s_tile + t, sh);
+            }
+            __threadfence();  // release these tiles' writes before counting them done
             __syncthreads();
-            if (S.kind < Q_DOT_B) cycle_tile<T, LP>(a, inst, S.kind, S.level, S.colour, s_tile);
-            else krylov_tile<T, LP>(a, inst, S, s_tile, sh);
-            __threadfence();  // release this tile's writes before counting it done
+            if (threadIdx.x == 0) s_last = atomicAdd(a.done + inst, s_cnt) + s_cnt == S.ntiles;
             __syncthreads();
-            if (threadIdx.x == 0) s_last = atomicAdd(a.done + inst, 1) == S.ntiles - 1;
-            __syncthreads();
-            if (s_last) handle<T>(a, inst, S, red, sh);
+            if (s_last) {
+                handle<T>(a, inst, S, red, sh);
+                if (threadIdx.x == 0) cached_inst = -1;  // S now holds the next phase's state
+            }
         } else if (threadIdx.x == 0) {
             __nanosleep(backoff);
             backoff = min(backoff * 2, 256);
@@ -704,10 +726,14 @@ static int queue_solve(Batch& B, QBuf& q, QArgs& a, int tpb, cudaStream_t s) {
     count_launches(2);
     kq_init<T><<<(B.count + 127) / 128, 128, 0, s>>>(a, tpb);
     // variant: loads through L1 (plain, made current by the acquire fences) or around it, and
-    // the register bound (2 or 3 resident CTAs of 256 threads per SM)
+    // the register bound (2 to 5 resident CTAs of 256 threads per SM; 4 and 5 spill)
     const char* ev = std::getenv("SDX_QUEUE_VARIANT");
     const int var = ev ? std::atoi(ev) : B.queue_variant;
-    void (*k)(QArgs) = var == 1 ? kq_solve<T, LD_PLAIN, 3> : (var == 2 ? kq_solve<T, LD_CG, 2> : kq_solve<T, LD_PLAIN, 2>);
+    void (*k)(QArgs) = var == 1 ? kq_solve<T, LD_PLAIN, 3>
+                     : var == 2 ? kq_solve<T, LD_CG, 2>
+                     : var == 3 ? kq_solve<T, LD_PLAIN, 4>
+                     : var == 4 ? kq_solve<T, LD_PLAIN, 5>
+                                : kq_solve<T, LD_PLAIN, 2>;
     int per_sm = 0;
     CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, tpb, 0));
     if (per_sm < 1) { set_error("persistent batch solver cannot launch"); throw Fail{SDX_ECUDA}; }
@@ -723,7 +749,7 @@ int bsolve_queue(Batch& B, const double* const* b, double* const* x, double rtol
     const int tpb = B.queue_tpb;
     if (m > QMAX_M || (int)B.lv.size() > QMAX_LEV) { set_error("restart or depth beyond the persistent solver's limits"); throw Fail{SDX_EINVAL}; }
     for (int i = 0; i < N; ++i)
-        if (4 * B.inst[i]->lv[0].nn / tpb + 1 >= (long long)W_MASK) { set_error("instance too large for the persistent solver"); throw Fail{SDX_EINVAL}; }
+        if (4 * B.inst[i]->lv[0].nn / tpb + 1 >= (long long)W_MASK - 65536) { set_error("instance too large for the persistent solver"); throw Fail{SDX_EINVAL}; }
     batch_ensure_krylov(B, m);
     QBuf* q = static_cast<QBuf*>(B.queue);
     if (q && (q->m < m || q->tpb != tpb)) { CK(cudaStreamSynchronize(s)); queue_free(B); q = nullptr; }
