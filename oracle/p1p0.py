@@ -24,10 +24,12 @@ that is exact for polynomials of degree 5 on every tetrahedron.
 from __future__ import annotations
 
 import numpy as np
+import scipy.linalg as sla
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
 from .forms import DIRICHLET, TRACTION, Discretisation, masked
+from .solvers import DENSE_LIMIT
 
 GAMMA = 1.0
 
@@ -148,14 +150,30 @@ class P1P0:
         free = np.flatnonzero(~con)
         Kff = K[free][:, free].tocsc()
         r = rhs[free]
-        if TRACTION not in self.disc.face:
-            w = np.zeros(3 * self.nn + self.nT)
-            w[3 * self.nn:] = self.pressure_weights()
-            wf = w[free]
-            Kb = sp.bmat([[Kff, sp.csc_matrix(wf[:, None])], [sp.csc_matrix(wf[None, :]), None]], format="csc")
-            sol = spla.spsolve(Kb, np.concatenate([r, [0.0]]))[: free.size]
+        nullspace = TRACTION not in self.disc.face
+        w = np.zeros(3 * self.nn + self.nT)
+        w[3 * self.nn:] = self.pressure_weights()
+        wf = w[free]
+        if free.size <= DENSE_LIMIT:
+            # bordered [[K_ff, w], [w^T, 0]]: also right for a right-hand side with a component
+            # along the constant pressure (lifted boundary data of non-zero discrete net flux)
+            M = Kff.toarray()
+            rr = r
+            if nullspace:
+                M = np.block([[M, wf[:, None]], [wf[None, :], np.zeros((1, 1))]])
+                rr = np.concatenate([r, [0.0]])
+            sol = sla.solve(M, rr)[: free.size]
+        elif nullspace:
+            # the constant pressure spans the null space: pin the last pressure DoF, then shift
+            # the pressures to w.p = 0 (the bordered system's solution for a consistent b)
+            keep = np.ones(free.size, dtype=bool)
+            keep[-1] = False
+            sol = np.zeros(free.size)
+            sol[keep] = spla.splu(sp.csc_matrix(Kff[keep][:, keep])).solve(r[keep])
+            pm = free >= 3 * self.nn
+            sol[pm] -= np.dot(wf[pm], sol[pm]) / wf[pm].sum()
         else:
-            sol = spla.spsolve(Kff, r)
+            sol = spla.splu(Kff).solve(r)
         x = xD.copy()
         x[free] = sol
         return x
