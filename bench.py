@@ -43,7 +43,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per side (workload size)")
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "levels", "guess", "batch", "paper", "conv"],
+    ap.add_argument("--mode", default="solve", choices=["solve", "sweep", "levels", "guess", "batch", "paper", "conv",
+                                                        "p1p0"],
                     help="sweep: only time the operator apply and smoother passes (profiling); "
                          "guess: only the learned-initial-guess experiment; batch: only the batched workload")
     ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32"], help="arithmetic of --mode sweep")
@@ -217,11 +218,12 @@ def main():
     if args.mode == "levels":
         run_levels(args)
         return
-    if args.mode in ("guess", "batch", "paper", "conv"):
+    if args.mode in ("guess", "batch", "paper", "conv", "p1p0"):
         import torch
         torch.cuda.set_device(0)
         from paper_1604_07994_gb300 import sdx
-        out = {"guess": run_guess, "batch": run_batch, "paper": run_paper, "conv": run_conv}[args.mode](args, sdx, torch)
+        out = {"guess": run_guess, "batch": run_batch, "paper": run_paper, "conv": run_conv,
+               "p1p0": run_p1p0}[args.mode](args, sdx, torch)
         print(json.dumps({"mode": args.mode, **out}), flush=True)
         return
     import torch
@@ -373,6 +375,9 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
     # algorithmic flops of one velocity colour pass (decoupled, per updated node):
     # 3 x (7-point Laplacian 8 + B^T p row 16 + update 4) + 7 shared p differences = 91
     out["roofline_kernel"] = {"ms": t_vel, "flops": 91.0 * half, "bytes": 58.0 * nn}
+    out["vcycle_levels_fp64"] = _guarded(lambda: level_gbs(level_times(H, sdx, torch, stream, "fp64")))
+    out["sweeps_fp32_decoupled"] = _guarded(lambda: fp32_sweeps(prob, xr, b, con, nn, stream, torch, sdx))
+    out["cube_inclusion_16"] = _guarded(lambda: run_cube16(sdx, torch, W, stream))
     # e2e: through the host-buffer entry point
     bh = b.cpu().numpy().copy()
     xh = np.zeros_like(bh)
@@ -419,6 +424,7 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
         out["learned_guess"] = _guarded(lambda: run_guess(args, sdx, torch))
     if not args.no_paper:
         out["paper_columns"] = _guarded(lambda: run_paper(args, sdx, torch))
+        out["p1p0"] = _guarded(lambda: run_p1p0(args, sdx, torch))
     if not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1:
         out["cpu_baseline"] = _guarded(oracle_sample)
     return out
@@ -826,6 +832,74 @@ def run_guess(args, sdx, torch):
     return out
 
 
+def level_gbs(rows):
+    """Algorithmic GB/s of the transfers per level (FP64): restriction reads the fine residual
+    (32 B per fine node) and writes the coarse right-hand side (32 B per coarse node);
+    prolongation reads the coarse correction (32 B per coarse node) and reads and writes the
+    fine iterate (64 B per fine node)."""
+    for l, row in enumerate(rows[:-1]):
+        nf, nc = row["nodes"], rows[l + 1]["nodes"]
+        if "restrict_ms" in row:
+            row["restrict_gbs"] = (32 * nf + 32 * nc) / (row["restrict_ms"] * 1e-3) / 1e9
+            row["prolong_gbs"] = (32 * nc + 64 * nf) / (row["prolong_ms"] * 1e-3) / 1e9
+    return rows
+
+
+def fp32_sweeps(prob, xr, b, con, nn, stream, torch, sdx, reps=20):
+    """The FP32 kernels of the refined solve's cycle on the finest level of the benchmark
+    workload: apply, red velocity pass, red pressure pass, with algorithmic GB/s (FP32 bytes
+    per node: apply 32 + 2, velocity pass 7 x 4 + 2, pressure pass 5.5 x 4 + 2) and the
+    velocity pass as an HBM roofline against the measured copy bandwidth."""
+    H = sdx.Hierarchy.from_problem(prob, form="tr", coarse_form="sym", prec=sdx.PREC_FP32_REFINED)
+    try:
+        x32 = xr.float()
+        b32 = b.float()
+        b32[con] = 0.0
+        y = torch.empty_like(x32)
+        xs = x32.clone()
+        t = {"apply": _time(lambda: H.sdx_apply_f32(0, x32, y), reps, stream, torch),
+             "velocity_pass": _time(lambda: H.sdx_smooth_pass_f32(0, 0, 0, b32, xs), reps, stream, torch),
+             "pressure_pass": _time(lambda: H.sdx_smooth_pass_f32(0, 1, 0, b32, xs), reps, stream, torch)}
+        xv = torch.zeros_like(x32)
+        bpn = {"apply": 34, "velocity_pass": 30, "pressure_pass": 24}
+        out = {k: {"ms": v, "bytes_per_node": bpn[k], "gbs": bpn[k] * nn / (v * 1e-3) / 1e9} for k, v in t.items()}
+        out["uzawa_step_ms"] = _time(lambda: H.sdx_uzawa_f32(0, b32, xs, 1), 5, stream, torch)
+        pk = peaks().get("hbm_gbs")
+        g = out["velocity_pass"]["gbs"]
+        out["roofline_fp32"] = {"bound": "hbm", "achieved": g, "peak": pk, "unit": "GB/s",
+                                "frac": g / pk if pk else None, "traffic": None,
+                                "kernel": "red FP32 velocity pass (special rows staged + k_vel_uniform<float, a_tr>)",
+                                "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy)"}
+        del xv
+        return out
+    finally:
+        H.close()
+
+
+def run_cube16(sdx, torch, W, stream):
+    """The 16^3 cube inclusion ([0.25, 0.75]^3, mu 10 inside, 1 outside, no-slip, manufactured
+    forcing), FP64 decoupled form: one operator apply and a solve to 1e-8 from zero."""
+    p = W.cube_inclusion(16, 4)
+    H = sdx.Hierarchy.from_problem(p, form="tr", coarse_form="sym", prec=sdx.PREC_FP64)
+    try:
+        _, nodes, free = H.sdx_level_size(0)
+        b = torch.zeros(4 * nodes, dtype=torch.float64, device="cuda")
+        H.sdx_rhs(torch.from_numpy(p.nodal_forcing().ravel()).cuda(), b)
+        y = torch.empty_like(b)
+        t_ap = _time(lambda: H.sdx_apply(0, b, y), 20, stream, torch)
+        x = torch.zeros_like(b)
+        st = {}
+
+        def solve():
+            x.zero_()
+            st.update(H.sdx_solve(b, x, rtol=1e-8, maxit=200, outer=sdx.OUTER_FGMRES, restart=30))
+        t_s = _time(solve, 5, stream, torch)
+        return {"cells": 16, "free_dofs": free, "apply_ms": t_ap, "time_to_1e8_ms": t_s,
+                "iterations": st["iterations"], "final_rel_res": st["res"] / st["bnorm"]}
+    finally:
+        H.close()
+
+
 def level_times(H, sdx, torch, stream, prec="fp64", reps=20):
     """CUDA-event times of the pieces of one V_var cycle on every level of a hierarchy: one
     Uzawa step (nu = 3 + 2l of them pre and post), the residual, restriction, prolongation, and
@@ -864,6 +938,85 @@ def level_times(H, sdx, torch, stream, prec="fp64", reps=20):
             row.update({"nu_steps_ms": t_st, "apply_ms": t_ap, "nu": nu,
                         "level_cycle_ms": 2 * t_st + t_ap})
         out.append(row)
+    return out
+
+
+def run_p1p0(args, sdx, torch, levels=(0, 1, 2, 3, 4, 5)):
+    """The P1-P0 scheme of Sec. 3 on the GPU: the Couette flow of Sec. 4.2.2 (mu1/mu2 = 1e3,
+    exact Dirichlet data lifted through the residual, gamma = 1) at levels 0-5 (4^3 to 128^3
+    cells): solve time, FGMRES iterations and the largest nodal velocity error against the
+    exact solution (second order: the ratio between levels tends to 4); and the columns
+    problem of Sec. 4.2.4 at 128^3: time to 1e-8, iterations and the largest element-wise mass
+    imbalance of the post-processed fluxes relative to the largest flux."""
+    from paper_1604_07994_gb300 import workloads as W
+    out = {"couette": {}}
+    prev = None
+    for lvl in levels:
+        n = 4 << lvl
+        c = (np.arange(n) + 0.5) / n
+        _, Y, _ = np.meshgrid(c, c, c, indexing="ij")  # [k, j, i]: y = j
+        ids = (Y >= 0.5).astype(np.uint8)
+        p = W.Problem(n=n, n_coarse=2 if n == 4 else 4, cell_id=ids, mu=np.array([1.0, 1e-3]),
+                      face=(0,) * 6, forcing=None, name=f"couette_{n}")
+        H = sdx.P1P0(p)
+        _, nodes, tets, free = H.size(0)
+        nn3 = 3 * nodes
+        g = np.arange(n + 1) / n
+        _, yy, xx = (a.ravel() for a in np.meshgrid(g, g, g, indexing="ij"))
+        u_ex = np.stack([0.5 * (1 - xx ** 2), xx * (yy - 0.5), 0 * xx]).ravel()
+        bnd = np.zeros((n + 1,) * 3, dtype=bool)
+        bnd[[0, -1]] = bnd[:, [0, -1]] = bnd[:, :, [0, -1]] = True
+        con = np.tile(bnd.ravel(), 3)  # every face Dirichlet: the boundary nodes' components
+        xD = np.concatenate([np.where(con, u_ex, 0.0), np.zeros(tets)])
+        # load f = (3 mu, 0, 0): nodal values are the mean over the cells around each node
+        mu_c = np.where(ids > 0, 1e-3, 1.0)
+        fn = np.zeros((n + 1,) * 3)
+        m = np.zeros((n + 1,) * 3)
+        for dk in (0, 1):
+            for dj in (0, 1):
+                for di in (0, 1):
+                    fn[dk:dk + n, dj:dj + n, di:di + n] += mu_c
+                    m[dk:dk + n, dj:dj + n, di:di + n] += 1.0
+        f = np.zeros((3, nodes))
+        f[0] = (3.0 * fn / m).ravel()
+        b = torch.zeros(nn3 + tets, dtype=torch.float64, device="cuda")
+        H.rhs(torch.from_numpy(f.ravel()).cuda(), b)
+        r = torch.empty_like(b)
+        H.residual(0, b, torch.from_numpy(xD).cuda(), r)
+        x = torch.zeros_like(b)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = H.solve(r, x, rtol=1e-10, maxit=400, restart=30)
+        torch.cuda.synchronize()
+        ts = time.perf_counter() - t0
+        uh = np.where(con, u_ex, x[:nn3].cpu().numpy())
+        err = float(np.abs(uh - u_ex).max())
+        row = {"cells": n, "free_dofs": free, "solve_s": ts, "iterations": st["iterations"],
+               "max_nodal_velocity_error": err}
+        if prev is not None:
+            row["error_ratio_to_coarser"] = prev / err
+        prev = err
+        out["couette"][f"L{lvl}"] = row
+    nc = 128 if args.n >= 128 else args.n
+    p = W.viscosity_columns(nc, 4)
+    H = sdx.P1P0(p, form="tr")
+    _, nodes, tets, free = H.size(0)
+    b = torch.zeros(3 * nodes + tets, dtype=torch.float64, device="cuda")
+    H.rhs(torch.from_numpy(p.nodal_forcing().ravel()).cuda(), b)
+    x = torch.zeros_like(b)
+    H.solve(b, x, rtol=1e-8, maxit=400, restart=30)
+    x.zero_()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st = H.solve(b, x, rtol=1e-8, maxit=400, restart=30)
+    torch.cuda.synchronize()
+    ts = time.perf_counter() - t0
+    flux = torch.empty(4 * tets, dtype=torch.float64, device="cuda")
+    bal = torch.empty(tets, dtype=torch.float64, device="cuda")
+    H.fluxes(x, flux, bal)
+    out["columns"] = {"cells": nc, "free_dofs": free, "time_to_1e8_s": ts, "gdofs": free / ts / 1e9,
+                      "iterations": st["iterations"],
+                      "max_element_imbalance_over_max_flux": float(bal.abs().max() / flux.abs().max())}
     return out
 
 

@@ -374,6 +374,50 @@ int sdx_guess_predict(sdx_hier_t h, sdx_net_t net, const double* f_nodal, double
  * ||b - K x|| <= ||b|| always holds.  Asynchronous.  Not for batch-owned hierarchies. */
 int sdx_guess_refine(sdx_hier_t h, const double* b, double* x, int steps, void* stream);
 
+/* ------------------------------------------------------------------ P1-P0 scheme
+ * The stabilised lowest-order pair of Sec. 3.1-3.2: P1 velocity (the same velocity block,
+ * forms, boundary conditions and hierarchy rules as above) and one pressure per tetrahedron,
+ * with the interior-penalty stabilisation of eq. (stabc),
+ *     c(p, q) = gamma sum_i 1/(2 mu_i) sum over the interior facets F of subdomain i of
+ *               |T1||T2| / (|T1| + |T2|) [p]_F [q]_F
+ * (no penalty across the viscosity interface or on the domain boundary; the paper uses
+ * gamma = 1, Sec. 4.2), and b(v, q) = -(div v, q).  Vectors are 3 (n+1)^3 velocity values
+ * (u_x, u_y, u_z as above) followed by 6 n^3 pressures, tetrahedron s of cell (i, j, k) at
+ * s * n^3 + i + n (j + n k), s the axis permutation of the Kuhn path c, c + e_s1, c + e_s1 + e_s2,
+ * c + (1,1,1) in the order (0,1,2), (0,2,1), (1,0,2), (1,2,0), (2,0,1), (2,1,0).  FP64 only.
+ * Solver: the V_var(3,3) Uzawa cycle with the red-black velocity smoother above and a relaxed
+ * Jacobi pressure step on the 1/mu-weighted P0 mass (p += 0.6 (mu_T / |T|) (B u - C p - g)_T),
+ * P0 pressures transferred by embedding a coarse tetrahedron into its eight children; FGMRES or
+ * plain cycles outside; direct coarsest solve (at most 12000 unknowns). */
+typedef struct sdx_p0* sdx_p0_t; /* opaque, library-owned */
+
+/* Build the hierarchy (desc->prec must be SDX_PREC_FP64; pspg_beta and coarse_correction
+ * are not used) with penalty constant gamma > 0.  Synchronous.  Errors as sdx_create. */
+int sdx_p0_create(const sdx_desc* desc, double gamma, sdx_p0_t* out);
+int sdx_p0_destroy(sdx_p0_t h);
+/* Cells per side, nodes, tetrahedra and free unknowns of one level. */
+int sdx_p0_size(sdx_p0_t h, int level, int* n, int64_t* nodes, int64_t* tets, int64_t* free_dofs);
+/* y = K x and r = b - K x on one level (device vectors of 3 (n+1)^3 + 6 n^3 doubles). */
+int sdx_p0_apply(sdx_p0_t h, int level, const double* x, double* y, void* stream);
+int sdx_p0_residual(sdx_p0_t h, int level, const double* b, const double* x, double* r, void* stream);
+/* Finest-level right-hand side: velocity rows as sdx_rhs (lumped mass times the nodal
+ * forcing), pressure rows zero (the interior-penalty form has no consistent load). */
+int sdx_p0_rhs(sdx_p0_t h, const double* f_nodal, double* b, void* stream);
+/* One Uzawa smoothing step on one level, in place on x. */
+int sdx_p0_uzawa(sdx_p0_t h, int level, const double* b, double* x, void* stream);
+/* One V-cycle on the finest level: x += M (b - K x). */
+int sdx_p0_vcycle(sdx_p0_t h, const double* b, double* x, void* stream);
+/* Solve as sdx_solve (same arguments and return codes). */
+int sdx_p0_solve(sdx_p0_t h, const double* b, double* x, double rtol, int maxit, int outer, int restart,
+                 sdx_stats* stats, void* stream);
+/* Local flux post-process (Sec. 3.2, remark after eq. stabc) of a finest-level vector x:
+ * flux[4 t + m] = int over the facet of tetrahedron t opposite its path vertex m of
+ * u_h . n_T + Delta j, Delta j integrated = gamma / (2 mu) |T||T_F| / (|T| + |T_F|) (p_T - p_F)
+ * on facets inside one viscosity (outward from t), and balance[t] = the sum of t's four
+ * fluxes, zero for a solution of the discrete problem (element-wise mass conservation).
+ * flux: 4 * 6 n^3 doubles, balance: 6 n^3 doubles (device). */
+int sdx_p0_fluxes(sdx_p0_t h, const double* x, double* flux, double* balance, void* stream);
+
 /* Number of CUDA kernels this library has launched in the process so far (all
  * hierarchies, all threads); used to count the kernels of a timed region. */
 int64_t sdx_kernel_launches(void);

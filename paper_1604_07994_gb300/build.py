@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libsdx.so")
-SOURCES = ["kernels.cu", "sdx.cu", "batch.cu", "batch_queue.cu", "nn.cu"]
+SOURCES = ["kernels.cu", "sdx.cu", "batch.cu", "batch_queue.cu", "nn.cu", "p1p0.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include")]

@@ -32,7 +32,8 @@ NOALLOC_MAX_ROWS = 65536
 EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_constraint_mask",
             "sdx_interface_mask", "sdx_apply", "sdx_residual", "sdx_rhs", "sdx_uzawa", "sdx_smooth_pass",
             "sdx_kernel_launches", "sdx_smooth_pass_noalloc", "sdx_apply_f32", "sdx_smooth_pass_f32",
-            "sdx_uzawa_f32",
+            "sdx_uzawa_f32", "sdx_p0_create", "sdx_p0_destroy", "sdx_p0_size", "sdx_p0_apply",
+            "sdx_p0_residual", "sdx_p0_rhs", "sdx_p0_uzawa", "sdx_p0_vcycle", "sdx_p0_solve", "sdx_p0_fluxes",
             "sdx_restrict", "sdx_prolong_add", "sdx_vcycle", "sdx_solve", "sdx_solve_host",
             "sdx_batch_create", "sdx_batch_destroy", "sdx_batch_size", "sdx_batch_shape", "sdx_batch_instance",
             "sdx_batch_vcycle", "sdx_batch_solve", "sdx_net_param_count", "sdx_net_create",
@@ -98,6 +99,16 @@ def _load_locked() -> ctypes.CDLL:
         "sdx_apply_f32": [P, I, P, P, P],
         "sdx_smooth_pass_f32": [P, I, I, I, P, P, P],
         "sdx_uzawa_f32": [P, I, P, P, I, P],
+        "sdx_p0_create": [ctypes.POINTER(sdx_desc), D, ctypes.POINTER(P)],
+        "sdx_p0_destroy": [P],
+        "sdx_p0_size": [P, I, ctypes.POINTER(I), ctypes.POINTER(L), ctypes.POINTER(L), ctypes.POINTER(L)],
+        "sdx_p0_apply": [P, I, P, P, P],
+        "sdx_p0_residual": [P, I, P, P, P, P],
+        "sdx_p0_rhs": [P, P, P, P],
+        "sdx_p0_uzawa": [P, I, P, P, P],
+        "sdx_p0_vcycle": [P, P, P, P],
+        "sdx_p0_solve": [P, P, P, D, I, I, I, ctypes.POINTER(sdx_stats), P],
+        "sdx_p0_fluxes": [P, P, P, P, P],
         "sdx_restrict": [P, I, P, P, P],
         "sdx_prolong_add": [P, I, P, P, P],
         "sdx_vcycle": [P, P, P, P],
@@ -369,6 +380,79 @@ class Hierarchy:
                                      int(maxit), int(outer), int(restart), ctypes.byref(st),
                                      _stream(stream)), allow)
         return st.as_dict()
+
+
+class P1P0:
+    """A hierarchy of the P1-P0 scheme (sdx_p0_*; owned, freed by close() or on deletion).
+    Vectors: 3 (n+1)^3 velocities then 6 n^3 pressures (tetrahedron s of cell c at s n^3 + c)."""
+
+    def __init__(self, problem, form="tr", coarse_form=None, gamma: float = 1.0, coarsening="resolved"):
+        lib = load()
+        d, self._keep = _make_desc(problem.n, problem.n_coarse, problem.cell_id, problem.mu, problem.face, form,
+                                   coarse_form, PREC_FP64, 1.0 / 12.0, None, False, coarsening)
+        h = ctypes.c_void_p()
+        _check(lib.sdx_p0_create(ctypes.byref(d), float(gamma), ctypes.byref(h)))
+        self._h = h
+        self.n = int(problem.n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sdx_p0_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def size(self, level: int = 0):
+        n, nodes, tets, free = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(load().sdx_p0_size(self._h, level, ctypes.byref(n), ctypes.byref(nodes), ctypes.byref(tets),
+                                  ctypes.byref(free)))
+        return n.value, nodes.value, tets.value, free.value
+
+    def _len(self, level: int) -> int:
+        _, nodes, tets, _ = self.size(level)
+        return 3 * nodes + tets
+
+    def apply(self, level, x, y, stream=None):
+        m = self._len(level)
+        px, py = _vecs((x, m), (y, m))
+        _check(load().sdx_p0_apply(self._h, level, px, py, _stream(stream)))
+
+    def residual(self, level, b, x, r, stream=None):
+        m = self._len(level)
+        pb, px, pr = _vecs((b, m), (x, m), (r, m))
+        _check(load().sdx_p0_residual(self._h, level, pb, px, pr, _stream(stream)))
+
+    def rhs(self, f, b, stream=None):
+        _, nodes, _, _ = self.size(0)
+        pf, pb = _vecs((f, 3 * nodes), (b, self._len(0)))
+        _check(load().sdx_p0_rhs(self._h, pf, pb, _stream(stream)))
+
+    def uzawa(self, level, b, x, stream=None):
+        m = self._len(level)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_p0_uzawa(self._h, level, pb, px, _stream(stream)))
+
+    def vcycle(self, b, x, stream=None):
+        m = self._len(0)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_p0_vcycle(self._h, pb, px, _stream(stream)))
+
+    def solve(self, b, x, rtol=1e-8, maxit=100, outer=OUTER_FGMRES, restart=30, stream=None) -> dict:
+        st = sdx_stats()
+        m = self._len(0)
+        pb, px = _vecs((b, m), (x, m))
+        _check(load().sdx_p0_solve(self._h, pb, px, float(rtol), int(maxit), int(outer), int(restart),
+                                   ctypes.byref(st), _stream(stream)))
+        return st.as_dict()
+
+    def fluxes(self, x, flux, balance, stream=None):
+        _, _, tets, _ = self.size(0)
+        px, pf, pbal = _vecs((x, self._len(0)), (flux, 4 * tets), (balance, tets))
+        _check(load().sdx_p0_fluxes(self._h, px, pf, pbal, _stream(stream)))
 
 
 def _ptr_array(vectors, itemsize=8):

@@ -1,0 +1,200 @@
+"""GPU parity of the P1-P0 scheme (sdx_p0_*: Sec. 3.1-3.2, P0 pressure, interior-penalty
+stabilisation eq. (stabc), flux post-process) against the oracle (oracle/p1p0.py).
+
+Tolerances as for the P1-P1 path: 1e-13 relative max-norm per operator apply and per flux
+evaluation, 1e-12 per smoothing step, 1e-10 per V-cycle (dense inverse against LU), 1e-8
+relative L2 per solve.  The oracle numbers tetrahedra permutation by permutation and, inside,
+in the order i-major of its mesh generator; the library stores tetrahedron s of cell
+i + n (j + n k) at s n^3 + cell - the tests permute between the two."""
+import numpy as np
+import pytest
+
+from tests._lib import ensure_built
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+from oracle.forms import DIRICHLET  # noqa: E402
+from oracle.p1p0 import P1P0 as OP1P0  # noqa: E402
+from oracle.p1p0 import P1P0Hierarchy, P1P0Level  # noqa: E402
+from paper_1604_07994_gb300 import workloads as W  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def sdx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    ensure_built()
+    from paper_1604_07994_gb300 import sdx as mod
+    return mod
+
+
+PROBLEMS = {
+    "cube16": lambda: W.cube_inclusion(16, 4),
+    "boxes16": lambda: W.three_boxes(16, 8, contrast=1e4),
+    "layer16": lambda: W.top_layer(16, 8),
+    "columns16": lambda: W.viscosity_columns(16, 4),
+    "tiny2": lambda: W.Problem(n=2, n_coarse=2,
+                               cell_id=np.array([[[0, 1], [1, 0]], [[1, 1], [0, 0]]], dtype=np.uint8),
+                               mu=np.array([1.0, 7.0]), face=(2, 0, 1, 2, 0, 1),
+                               forcing=W.gaussian_blobs(1), name="tiny2"),
+}
+
+
+def _perm(n):
+    """gpu_of_oracle[T]: library index of oracle tetrahedron T."""
+    n3 = n ** 3
+    T = np.arange(6 * n3)
+    s, r = np.divmod(T, n3)
+    ci, r = np.divmod(r, n * n)
+    cj, ck = np.divmod(r, n)
+    return s * n3 + ci + n * (cj + n * ck)
+
+
+def to_gpu(x, n):
+    nn = (n + 1) ** 3
+    out = x.copy()
+    out[3 * nn + _perm(n)] = x[3 * nn:]
+    return out
+
+
+def to_oracle(x, n):
+    nn = (n + 1) ** 3
+    out = x.copy()
+    out[3 * nn:] = x[3 * nn + _perm(n)]
+    return out
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()
+
+
+def _host(t):
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def _rand(L, seed):
+    rng = np.random.Generator(np.random.PCG64(seed))
+    x = rng.uniform(-1, 1, 3 * L.nn + L.nT)
+    x[L.con] = 0.0
+    return x
+
+
+def _relmax(a, b):
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+@pytest.mark.parametrize("form", ["tr", "sym", "grad"])
+@pytest.mark.parametrize("name", list(PROBLEMS))
+def test_p0_apply_and_step_match_oracle(sdx, name, form):
+    p = PROBLEMS[name]()
+    L = P1P0Level(p.n, p.cell_mu().ravel(), p.face, form)
+    H = sdx.P1P0(p, form=form)
+    x = _rand(L, 3)
+    y = _dev(np.zeros_like(x))
+    H.apply(0, _dev(to_gpu(x, p.n)), y)
+    assert _relmax(to_oracle(_host(y), p.n), L.K @ x) <= 1e-13
+    b = _rand(L, 4)
+    xd = _dev(to_gpu(x, p.n))
+    H.uzawa(0, _dev(to_gpu(b, p.n)), xd)
+    xo = x.copy()
+    L.uzawa(xo, b)
+    assert _relmax(to_oracle(_host(xd), p.n), xo) <= 1e-12
+
+
+@pytest.mark.parametrize("name,coarse_form", [("cube16", None), ("columns16", None), ("columns16", "sym"),
+                                              ("boxes16", "sym"), ("layer16", None)])
+def test_p0_vcycle_matches_oracle(sdx, name, coarse_form):
+    p = PROBLEMS[name]()
+    OH = P1P0Hierarchy(p.n, p.n_coarse, p.cell_mu().ravel(), p.face, "tr", coarse_form=coarse_form)
+    b = OH.levels[0].sp.rhs(p.nodal_forcing())
+    H = sdx.P1P0(p, form="tr", coarse_form=coarse_form)
+    bd = _dev(np.zeros_like(b))
+    H.rhs(_dev(p.nodal_forcing().ravel()), bd)
+    assert _relmax(to_oracle(_host(bd), p.n), b) <= 1e-13
+    xd = _dev(np.zeros_like(b))
+    xo = np.zeros_like(b)
+    for _ in range(2):
+        H.vcycle(bd, xd)
+        _oracle_vcycle_inplace(OH, xo, b)
+        assert np.linalg.norm(to_oracle(_host(xd), p.n) - xo) <= 1e-10 * np.linalg.norm(xo)
+
+
+def _oracle_vcycle_inplace(OH, x, b):
+    """x += M (b - K x), as sdx_p0_vcycle."""
+    L = OH.levels[0]
+    r = L.residual(x, b)
+    x += OH.vcycle(np.zeros_like(r), r)
+
+
+_direct = {}
+
+
+@pytest.mark.parametrize("outer", [0, 1])
+@pytest.mark.parametrize("name", ["cube16", "columns16", "layer16"])
+def test_p0_solve_matches_direct_and_conserves_mass(sdx, name, outer):
+    p = PROBLEMS[name]()
+    if name not in _direct:  # one sparse LU per problem (tens of seconds at 16^3)
+        O = OP1P0(p.n, p.cell_mu().ravel(), p.face)
+        b = O.rhs(p.nodal_forcing())
+        _direct[name] = (O, b, O.solve(b, "tr"))
+    O, b, xo = _direct[name]
+    H = sdx.P1P0(p, form="tr")
+    xd = _dev(np.zeros_like(b))
+    st = H.solve(_dev(to_gpu(b, p.n)), xd, rtol=1e-12, maxit=300, outer=outer, restart=40)
+    assert st["res"] <= 1e-12 * st["bnorm"]
+    x = to_oracle(_host(xd), p.n)
+    if 2 not in p.face:  # no traction face: pressure fixed up to a constant
+        w = O.pressure_weights()
+        x[3 * O.nn:] -= np.dot(w, x[3 * O.nn:]) / w.sum()
+    assert np.linalg.norm(x - xo) <= 1e-8 * np.linalg.norm(xo)
+    flux = torch.empty(4 * O.nT, dtype=torch.float64, device="cuda")
+    bal = torch.empty(O.nT, dtype=torch.float64, device="cuda")
+    H.fluxes(xd, flux, bal)
+    f, g = _host(flux), _host(bal)
+    assert np.abs(g).max() <= 1e-10 * np.abs(f).max()  # element-wise mass balance (solve to 1e-12)
+
+
+@pytest.mark.parametrize("name", ["cube16", "layer16", "tiny2"])
+def test_p0_flux_balance_matches_oracle_on_any_state(sdx, name):
+    """For an arbitrary state the per-element sum of the post-processed fluxes is
+    |T| div u_h + sum over penalised facets of w (p_T - p_F): the library's kernel against the
+    oracle's facet-based evaluation, at 1e-13."""
+    p = PROBLEMS[name]()
+    O = OP1P0(p.n, p.cell_mu().ravel(), p.face)
+    L = P1P0Level(p.n, p.cell_mu().ravel(), p.face)
+    x = _rand(L, 9)
+    H = sdx.P1P0(p)
+    flux = torch.empty(4 * O.nT, dtype=torch.float64, device="cuda")
+    bal = torch.empty(O.nT, dtype=torch.float64, device="cuda")
+    H.fluxes(_dev(to_gpu(x, p.n)), flux, bal)
+    g = _host(bal)[_perm(p.n)]
+    assert _relmax(g, O.element_balance(x)) <= 1e-13
+
+
+def test_p0_couette_errors_match_oracle(sdx):
+    """Sec. 4.2.2 Couette flow (exact Dirichlet data lifted through the residual) at levels 0-1:
+    the GPU solution's errors equal the oracle's direct solution's to 1e-7 relative."""
+    for n in (4, 8):
+        c = (np.arange(n) + 0.5) / n
+        _, Y, _ = np.meshgrid(c, c, c, indexing="ij")
+        ids = (Y >= 0.5).astype(np.uint8)
+        p = W.Problem(n=n, n_coarse=n // 2 if n > 4 else 2, cell_id=ids, mu=np.array([1.0, 1e-3]),
+                      face=(DIRICHLET,) * 6, forcing=None, name=f"couette_{n}")
+        O = OP1P0(n, p.cell_mu().ravel(), p.face)
+        fc = np.zeros((3, n ** 3))
+        fc[0] = 3.0 * p.cell_mu().ravel()
+        b = O.rhs(f_cell=fc)
+        xx, yy, _ = O.disc.xyz.T
+        xD = np.concatenate([np.stack([0.5 * (1 - xx ** 2), xx * (yy - 0.5), 0 * xx]).ravel(), np.zeros(O.nT)])
+        xo = O.solve(b, "tr", xD)
+        H = sdx.P1P0(p)
+        r = _dev(np.zeros_like(b))
+        xDc = np.where(O.constrained(), xD, 0.0)  # the lifting: boundary values only
+        H.residual(0, _dev(to_gpu(b, n)), _dev(to_gpu(xDc, n)), r)
+        xd = _dev(np.zeros_like(b))
+        H.solve(r, xd, rtol=1e-13, maxit=300, restart=40)
+        x = to_oracle(_host(xd), n) + np.where(O.constrained(), xD, 0.0)
+        x[3 * O.nn:] -= np.sum(O.vol * x[3 * O.nn:]) / O.vol.sum() - np.sum(O.vol * xo[3 * O.nn:]) / O.vol.sum()
+        assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
