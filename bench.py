@@ -29,7 +29,7 @@ sys.path.insert(0, ROOT)
 FP64_PEAK_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per clock per SM (GB300: 1.25 TFLOP/s FP64 nominal)
 # DRAM bytes (read + write) of one launch of the red FP64 velocity pass on the 128^3 workload,
 # from the ncu capture summarised in profiles/k_vel_uniform_three_boxes_128.md
-VEL_PASS_DRAM_BYTES_128 = 125037312 + 16562432
+VEL_PASS_DRAM_BYTES_128 = 124926208 + 14599424
 N_SM = 152
 SM_MAX_MHZ = 2070.0
 

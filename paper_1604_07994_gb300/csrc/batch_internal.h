@@ -104,7 +104,7 @@ struct Batch {
     void* queue = nullptr;
     int queue_tpb = 256;
     int queue_ctas_per_sm = 0;   // 0: as many as fit
-    int queue_variant = 1;       // 0: plain loads, 2 CTAs/SM; 1: plain, 3 CTAs/SM (default); 2: L2-only loads; 3, 4: plain, 4 / 5 CTAs/SM
+    int queue_variant = 3;       // 0: plain loads, 2 CTAs/SM; 1: plain, 3 CTAs/SM; 2: L2-only loads; 3 (default, fastest measured), 4: plain, 4 / 5 CTAs/SM
 };
 
 // Helpers of batch.cu used by the persistent solver.

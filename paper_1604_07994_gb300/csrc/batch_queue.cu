@@ -725,6 +725,9 @@ static int queue_solve(Batch& B, QBuf& q, QArgs& a, int tpb, cudaStream_t s) {
     fill_levels<T>(B, a);
     count_launches(2);
     kq_init<T><<<(B.count + 127) / 128, 128, 0, s>>>(a, tpb);
+    // test hook for the bounded wait: every instance's work word says "no tiles", so no CTA
+    // finds work, nothing progresses, and each CTA leaves when its wait runs out
+    if (std::getenv("SDX_TEST_QUEUE_STALL")) CK(cudaMemsetAsync(a.word, 0, sizeof(unsigned long long) * B.count, s));
     // variant: loads through L1 (plain, made current by the acquire fences) or around it, and
     // the register bound (2 to 5 resident CTAs of 256 threads per SM; 4 and 5 spill)
     const char* ev = std::getenv("SDX_QUEUE_VARIANT");

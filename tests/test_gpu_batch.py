@@ -235,3 +235,25 @@ def test_queue_solver_is_deterministic_and_matches_lockstep_iterations(sdx, monk
     assert runs[0][1] == runs[1][1]
     for iq, il in zip(runs[0][1], runs[2][1]):
         assert abs(iq - il) <= 1
+
+
+def test_queue_solver_stall_times_out_and_batch_recovers(sdx, monkeypatch):
+    """A test hook (SDX_TEST_QUEUE_STALL) clears every instance's work word after
+    initialisation, so no CTA of the persistent launch ever finds a tile: each waits without
+    progress until its bounded wait (about 4e9 clock cycles) ends, the solve returns
+    SDX_ETIMEOUT, and the next solve on the same batch converges."""
+    monkeypatch.delenv("SDX_BATCH_LOCKSTEP", raising=False)
+    probs = _small_batch()[:3]
+    B = sdx.Batch(probs, form="tr", coarse_form="sym", prec=0)
+    bs = [_dev(_rhs(p)[0]) for p in probs]
+    xs = [torch.zeros_like(b) for b in bs]
+    monkeypatch.setenv("SDX_TEST_QUEUE_STALL", "1")
+    with pytest.raises(sdx.SdxError) as e:
+        B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=100, restart=30)
+    assert e.value.code == sdx.ETIMEOUT
+    monkeypatch.delenv("SDX_TEST_QUEUE_STALL")
+    xs = [torch.zeros_like(b) for b in bs]
+    st = B.sdx_batch_solve(bs, xs, rtol=1e-8, maxit=100, restart=30)
+    for s in st:
+        assert s["res"] <= 1e-8 * s["bnorm"]
+    B.close()
