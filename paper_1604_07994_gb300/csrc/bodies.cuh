@@ -212,6 +212,24 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
 
 // ------------------------------------------------------------------ smoother passes
 // Velocity update of one non-special node (i, j, k): u_j += (f_j - (A u + B^T p)_j) / diag.
+// New velocities of a uniform node in the a_tr / gradient forms (mu-weighted 7-point Laplacian
+// block): u_j = S_j / 6 + idA f_j + a1 A_j(p) + a2 A_pair(j)(p) + a3 D(p), where S_j sums the six
+// axis neighbours of u_j (um / up: minus / plus neighbours along x, y, z) and A, D are the
+// pressure differences of bt_diffs.  Every kernel that updates these rows evaluates this one
+// expression, so they agree to the bit.
+template <typename T>
+__device__ __forceinline__ void vel_lap_update(const T pm[7], const T pp[7], const T um[3][3], const T up[3][3],
+                                               const T fv[3], T idA, T a1, T a2, T a3, T v[3]) {
+    const int pair[3] = {EYZ, EXZ, EXY};
+    T A[7];
+    const T aD = a3 * bt_diffs(pm, pp, A);
+#pragma unroll
+    for (int jj = 0; jj < 3; ++jj) {
+        const T s = ((um[jj][0] + up[jj][0]) + (um[jj][1] + up[jj][1])) + (um[jj][2] + up[jj][2]);
+        v[jj] = fma(s, T(1.0 / 6.0), fma(idA, fv[jj], fma(a1, A[jj], fma(a2, A[pair[jj]], aD))));
+    }
+}
+
 // For a_tr and the gradient form the uniform row is mu h (6 u_j - S_j) + (B^T p)_j with S_j the
 // sum of the six axis neighbours and diag = 6 mu h, so the update does not depend on the old
 // u_j: u_j = S_j / 6 + (f_j - (B^T p)_j) / (6 mu h); these rows read only velocities of the other
@@ -263,14 +281,10 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
             fv[c] = ldx<LP>(f + c * nn + node);
         }
         if (inf & INFO_SPECIAL) return;
-        const T idA = L.idA[id], a1 = L.a1[id], a2 = L.a2[id], a3 = L.a3[id];
-        T A[7];
-        const T aD = a3 * bt_diffs(pm, pp, A);
+        T v[3];
+        vel_lap_update(pm, pp, um, up, fv, L.idA[id], L.a1[id], L.a2[id], L.a3[id], v);
 #pragma unroll
-        for (int jj = 0; jj < 3; ++jj) {
-            const T s = ((um[jj][0] + up[jj][0]) + (um[jj][1] + up[jj][1])) + (um[jj][2] + up[jj][2]);
-            x[jj * nn + node] = fma(s, T(1.0 / 6.0), fma(idA, fv[jj], fma(a1, A[jj], fma(a2, A[pair[jj]], aD))));
-        }
+        for (int jj = 0; jj < 3; ++jj) x[jj * nn + node] = v[jj];
     }
 }
 
@@ -282,6 +296,17 @@ __device__ __forceinline__ void vel_copy_node(const LevelView<T>& L, int i, int 
     if (L.info[node] & INFO_SPECIAL) return;
 #pragma unroll
     for (int c = 0; c < 3; ++c) x[c * L.nn + node] = ldx<LP>(src + c * L.nn + node);
+}
+
+// New pressure of a uniform node: (1 - omega) p + (omega / 6) S_p + k12 (2 diag + T)(u) - idC g,
+// with S_p the sum of the six axis neighbours of p and the B u sums of bu_sums over the 14 Kuhn
+// neighbours of the three velocity components (um / up: minus / plus).  Shared by every kernel
+// that updates these rows, so they agree to the bit.
+template <typename T>
+__device__ __forceinline__ T pre_update(const T um[3][7], const T up[3][7], T pc, T sp, T gv, T idC, T k12) {
+    T tsum, dsum;
+    bu_sums(um, up, tsum, dsum);
+    return fma(k12, fma(T(2), dsum, tsum), fma(-idC, gv, fma(T(OMEGA / 6.0), sp, T(1.0 - OMEGA) * pc)));
 }
 
 // Pressure Gauss-Seidel on C p = B u - g with relaxation OMEGA at one non-special node:
@@ -306,10 +331,7 @@ __device__ __forceinline__ void pre_uniform_node(const LevelView<T>& L, int i, i
                  (ldx<LP>(p + node - L.s2) + ldx<LP>(p + node + L.s2));
     const T gv = ldx<LP>(g + node);
     if (inf & INFO_SPECIAL) return;
-    T tsum, dsum;
-    bu_sums(um, up, tsum, dsum);
-    const T idC = L.idC[id], k12 = L.k12[id];
-    p[node] = fma(k12, fma(T(2), dsum, tsum), fma(-idC, gv, fma(T(OMEGA / 6.0), sp, T(1.0 - OMEGA) * pc)));
+    p[node] = pre_update(um, up, pc, sp, gv, L.idC[id], L.k12[id]);
 }
 
 // ------------------------------------------------------------------ special rows
