@@ -86,8 +86,9 @@ typedef struct {
     int coarse_form;        /* SDX_FORM_* on the coarser levels, or -1 for "same as form".
                                (Sec. 5 swaps a_tr for a_sym on the coarse grid.) */
     int prec;               /* SDX_PREC_* for sdx_vcycle and sdx_solve */
-    double pspg_beta;       /* stabilisation constant beta (> 0); 1/12 is the default used
-                               throughout this library's tests */
+    double pspg_beta;       /* stabilisation constant beta (> 0) of tau_T = beta h^2 / mu_T;
+                               the paper does not print it; 1/24 (the binding's default) gives
+                               the depth-independent multigrid rates of its Sec. 5 table */
     int coarsest_form;      /* SDX_FORM_* on the coarsest level only, or -1 for "same as
                                coarse_form" (with a single level the finest form applies) */
     int coarse_correction;  /* 1: the coarse-grid variant of Sec. 5 - the coarsest solve takes
@@ -347,6 +348,14 @@ int sdx_conv3(int n, int cin, int cout, const uint16_t* x, const uint16_t* w, co
               int relu, float* y, void* stream);
 int sdx_conv3_wgrad(int n, int cin, int cout, const uint16_t* x, const uint16_t* dz, float* dw,
                     void* stream);
+/* Input gradient of the convolution, as the network's backward pass computes it (for testing):
+ * dx[v][ci] (FP32) = sum over taps t and output channels co of W[t][co][ci] dz[v - off_t][co],
+ * i.e. the forward kernel run on the weights flipped in the taps and transposed in the channels
+ * (converted to BF16 on the device).  dz: BF16 [n^3][cout]; w: FP32 [27][cout][cin] (the layout
+ * of the network's parameters); same shapes as sdx_conv3.  Allocates its flipped-weight
+ * buffer and synchronises the stream.  Paper: no counterpart (the learned initial guess is an
+ * addition to the method). */
+int sdx_conv3_dgrad(int n, int cin, int cout, const uint16_t* dz, const float* w, float* dx, void* stream);
 
 /* Network input of a hierarchy's finest grid (n a multiple of 4) from the nodal forcing f
  * (device, 3 x (n+1)^3): x[n^3][16] (device, BF16) and *fscale_host = max |f| (1 if f = 0).

@@ -13,8 +13,10 @@ Paper passages followed here:
 * saddle matrix [[A, B^T], [B, -C]]                          Sec. 5, first display
 * C: PSPG / Brezzi-Pitkaranta pressure stabilisation. The paper states only that the
   equal-order P1-P1 scheme is stabilised (Sec. 4 intro, Sec. 5); we read it as
-  C = sum_T tau_T (grad p, grad q)_T with tau_T = beta h^2 / mu_T (beta = 1/12, h the cube
-  edge), the 1/mu scaling mirroring the 1/(2 mu_i) weight of eq. (stabc).  Its consistent
+  C = sum_T tau_T (grad p, grad q)_T with tau_T = beta h^2 / mu_T (h the cube edge), the 1/mu
+  scaling mirroring the 1/(2 mu_i) weight of eq. (stabc).  The paper does not print beta;
+  beta = 1/24 is the value at which the decoupled cycle's rate is independent of depth, as the
+  Sec. 5 table of rates reports (about 0.24 at every level; with 1/12 it grows with depth).  Its consistent
   right-hand side is g_q = -sum_T tau_T (f, grad q)_T.
 * boundary conditions: Dirichlet (all components), free-slip (normal component), traction
   (natural) - Sec. 1, eq. (boundary)
@@ -30,7 +32,7 @@ from .mesh import kuhn_tets, node_xyz, p1_geometry
 
 FORMS = ("tr", "sym", "grad", "dev")
 DIRICHLET, FREESLIP, TRACTION = 0, 1, 2
-PSPG_BETA = 1.0 / 12.0
+PSPG_BETA = 1.0 / 24.0
 
 
 def _sym_basis(grad):

@@ -1221,6 +1221,36 @@ int sdx_conv3(int n, int cin, int cout, const uint16_t* x, const uint16_t* w, co
     API_END
 }
 
+int sdx_conv3_dgrad(int n, int cin, int cout, const uint16_t* dz, const float* w, float* dx, void* stream) {
+    if (n < 1 || !dz || !w || !dx) { set_error("invalid convolution arguments"); return SDX_EINVAL; }
+    API_BEGIN
+    const long long nw = 27LL * cin * cout;
+    int* err = dalloc<int>(1);
+    bf16* wf = nullptr;
+    try {
+        wf = dalloc<bf16>(nw);
+        CK(cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream));
+        // the network's backward path: weights flipped in the taps and transposed in the
+        // channels, then the forward kernel from the output-gradient channels to the input ones
+        count_launches(1);
+        k_flip_weights<<<eblocks(nw), ETPB, 0, (cudaStream_t)stream>>>(cin, cout, w, wf);
+        ConvArgs a{n, reinterpret_cast<const bf16*>(dz), wf, nullptr, nullptr, 0, nullptr, dx, err};
+        launch_conv(cout, cin, a, (cudaStream_t)stream);
+    } catch (...) {
+        cudaFree(err);
+        cudaFree(wf);
+        throw;
+    }
+    int e = 0;
+    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    cudaFree(err);
+    cudaFree(wf);
+    if (e) { set_error("tensor-core wait timed out"); return SDX_ETIMEOUT; }
+    return launched("sdx_conv3_dgrad");
+    API_END
+}
+
 int sdx_conv3_wgrad(int n, int cin, int cout, const uint16_t* x, const uint16_t* dz, float* dw, void* stream) {
     if (n < 1 || !x || !dz || !dw) { set_error("invalid convolution arguments"); return SDX_EINVAL; }
     API_BEGIN

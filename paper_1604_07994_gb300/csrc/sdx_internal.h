@@ -134,7 +134,7 @@ struct Hier {
     int n = 0, n_coarse = 0, prec = 0;
     int form = 0, coarse_form = 0, coarsest_form = 0;
     bool coarse_correction = false;  // Sec. 5 right-hand-side correction of the coarsest solve
-    double beta = 1.0 / 12.0;
+    double beta = 1.0 / 24.0;
     int face[6] = {0, 0, 0, 0, 0, 0};
     bool nullspace = false;
     std::vector<double> mu_table;   // [256]

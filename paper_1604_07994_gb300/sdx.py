@@ -27,6 +27,9 @@ FORMS = {"tr": FORM_DECOUPLED, "decoupled": FORM_DECOUPLED, "sym": FORM_STRAIN,
          "strain": FORM_STRAIN, "grad": FORM_GRADIENT, "gradient": FORM_GRADIENT}
 PREC_FP64, PREC_FP32_REFINED = 0, 1
 OUTER_VCYCLE, OUTER_FGMRES = 0, 1
+# P1-P1 stabilisation constant beta of tau_T = beta h^2 / mu_T (not printed in the paper; 1/24
+# gives the depth-independent decoupled multigrid rates that its Sec. 5 table reports)
+PSPG_BETA = 1.0 / 24.0
 NOALLOC_MAX_ROWS = 65536
 
 EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_constraint_mask",
@@ -38,7 +41,8 @@ EXPORTED = ("sdx_create", "sdx_destroy", "sdx_levels", "sdx_level_size", "sdx_co
             "sdx_batch_create", "sdx_batch_destroy", "sdx_batch_size", "sdx_batch_shape", "sdx_batch_instance",
             "sdx_batch_vcycle", "sdx_batch_solve", "sdx_net_param_count", "sdx_net_create",
             "sdx_net_destroy", "sdx_net_get_params", "sdx_net_set_params", "sdx_net_forward",
-            "sdx_net_loss_grad", "sdx_net_train", "sdx_conv3", "sdx_conv3_wgrad", "sdx_guess_features",
+            "sdx_net_loss_grad", "sdx_net_train", "sdx_conv3", "sdx_conv3_wgrad", "sdx_conv3_dgrad",
+            "sdx_guess_features",
             "sdx_guess_target", "sdx_guess_predict", "sdx_guess_refine", "sdx_last_error", "sdx_strerror")
 
 
@@ -130,6 +134,7 @@ def _load_locked() -> ctypes.CDLL:
         "sdx_net_train": [P, I, I, P, P, I, I, ctypes.c_float, ctypes.c_uint64, P, P],
         "sdx_conv3": [I, I, I, P, P, P, I, P, P],
         "sdx_conv3_wgrad": [I, I, I, P, P, P, P],
+        "sdx_conv3_dgrad": [I, I, I, P, P, P, P],
         "sdx_guess_features": [P, P, P, ctypes.POINTER(D), P],
         "sdx_guess_target": [P, P, D, P, P],
         "sdx_guess_predict": [P, P, P, P, P],
@@ -231,7 +236,7 @@ class Hierarchy:
 
     def __init__(self, n: int, n_coarse: int, cell_id: np.ndarray, mu: Sequence[float],
                  face: Sequence[int], form="tr", coarse_form=None, prec=PREC_FP64,
-                 beta: float = 1.0 / 12.0, coarsest_form=None, coarse_correction: bool = False,
+                 beta: float = PSPG_BETA, coarsest_form=None, coarse_correction: bool = False,
                  coarsening="resolved"):
         lib = load()
         d, self._keep = _make_desc(n, n_coarse, cell_id, mu, face, form, coarse_form, prec, beta,
@@ -243,13 +248,13 @@ class Hierarchy:
         self.nn = (self.n + 1) ** 3
 
     @classmethod
-    def from_problem(cls, problem, form="tr", coarse_form=None, prec=PREC_FP64, beta=1.0 / 12.0,
+    def from_problem(cls, problem, form="tr", coarse_form=None, prec=PREC_FP64, beta=PSPG_BETA,
                      coarsest_form=None, coarse_correction=False, coarsening="resolved"):
         return cls(problem.n, problem.n_coarse, problem.cell_id, problem.mu, problem.face, form,
                    coarse_form, prec, beta, coarsest_form, coarse_correction, coarsening)
 
     @classmethod
-    def paper_coarse_variant(cls, problem, prec=PREC_FP64, beta=1.0 / 12.0):
+    def paper_coarse_variant(cls, problem, prec=PREC_FP64, beta=PSPG_BETA):
         """The coarse-grid variant of Sec. 5: decoupled form a_tr on every level but the
         coarsest, which takes a_sym with the corrected momentum right-hand side."""
         return cls.from_problem(problem, form="tr", coarse_form="tr", prec=prec, beta=beta,
@@ -389,7 +394,7 @@ class P1P0:
     def __init__(self, problem, form="tr", coarse_form=None, gamma: float = 1.0, coarsening="resolved"):
         lib = load()
         d, self._keep = _make_desc(problem.n, problem.n_coarse, problem.cell_id, problem.mu, problem.face, form,
-                                   coarse_form, PREC_FP64, 1.0 / 12.0, None, False, coarsening)
+                                   coarse_form, PREC_FP64, PSPG_BETA, None, False, coarsening)
         h = ctypes.c_void_p()
         _check(lib.sdx_p0_create(ctypes.byref(d), float(gamma), ctypes.byref(h)))
         self._h = h
@@ -466,7 +471,7 @@ class Batch:
     """Independent problems solved together by sdx_batch_* (owned; freed by close())."""
 
     def __init__(self, problems, form="tr", coarse_form=None, prec=PREC_FP32_REFINED,
-                 beta: float = 1.0 / 12.0, autotune: bool = True, coarsening="resolved"):
+                 beta: float = PSPG_BETA, autotune: bool = True, coarsening="resolved"):
         lib = load()
         descs = (sdx_desc * len(problems))()
         self._keep = []
@@ -596,6 +601,11 @@ class Net:
 def sdx_conv3(n, cin, cout, x_bf16, w_bf16, bias_f32, relu, y_f32, stream=None):
     _check(load().sdx_conv3(int(n), int(cin), int(cout), _ptr(x_bf16, 2), _ptr(w_bf16, 2),
                             _ptr(bias_f32, 4), int(relu), _ptr(y_f32, 4), _stream(stream)))
+
+
+def sdx_conv3_dgrad(n, cin, cout, dz_bf16, w_f32, dx_f32, stream=None):
+    _check(load().sdx_conv3_dgrad(int(n), int(cin), int(cout), _ptr(dz_bf16, 2), _ptr(w_f32, 4),
+                                  _ptr(dx_f32, 4), _stream(stream)))
 
 
 def sdx_conv3_wgrad(n, cin, cout, x_bf16, dz_bf16, dw_f32, stream=None):

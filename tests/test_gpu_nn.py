@@ -89,6 +89,24 @@ def test_conv3_wgrad_matches_oracle(sdx, cin, cout):
     assert np.abs(dw.cpu().numpy() - ref).max() <= 1e-3 * np.abs(ref).max()
 
 
+@pytest.mark.parametrize("cin,cout", SHAPES)
+def test_conv3_dgrad_matches_oracle(sdx, cin, cout):
+    """Input gradient as the backward pass forms it (flipped, transposed weights rounded to
+    BF16, then the forward kernel), element by element against the oracle's adjoint of conv3
+    with the same BF16-rounded weights: FP32 accumulation of at most 27 x 64 BF16 products,
+    1e-3 of the largest entry as for the forward kernel."""
+    n = 12
+    r = _rng(11 * cin + cout)
+    dzd, dz = _bf16(r.standard_normal((n ** 3, cout)))
+    wf = (r.standard_normal((27, cout, cin)) / np.sqrt(27 * cout)).astype(np.float32)
+    wd = torch.from_numpy(wf).cuda()
+    w_bf = torch.from_numpy(wf).to(torch.bfloat16).float().numpy().astype(np.float64)
+    dx = torch.zeros((n ** 3, cin), dtype=torch.float32, device="cuda")
+    sdx.sdx_conv3_dgrad(n, cin, cout, dzd, wd, dx)
+    ref = ON.conv3_dgrad(dz, w_bf, n)
+    assert np.abs(dx.cpu().numpy() - ref).max() <= 1e-3 * np.abs(ref).max()
+
+
 def _flat(params):
     return np.concatenate([np.concatenate([params[name][0].ravel(), params[name][1]]) for name, *_ in ON.LAYERS])
 
@@ -197,12 +215,16 @@ def test_guess_refine_matches_oracle(sdx):
 
 
 def test_trained_guess_against_zero_start(sdx):
-    """What the trained network gains over the method without it, on unseen instances: the
-    network is trained on solves the batched multigrid produced (16^3, 64 instances), its
-    training loss must drop, and solves from the refined guess must reach the same absolute
-    residual as solves from zero with a start no worse than zero (||b - K x0|| <= ||b||).  The
-    iteration counts of both starts are recorded; the guess is not required to save any (on
-    these grids it saves none: its residual is dominated by high-frequency error)."""
+    """What the trained network gains over the method without it, on unseen instances, asserted
+    as measured.  The network is trained on solves the batched multigrid produced (16^3, 64
+    instances) and its training loss must drop.  Solves from the refined guess must reach the
+    same tolerance as solves from zero, from a start no worse than zero (||b - K x0|| <= ||b||).
+    The measured gain is no iteration saved: the iteration count equals the zero start's, give
+    or take one.  On these 16^3 instances the refined start can have about half the zero start's
+    residual (0.55 measured on the first; on the 128^3 layouts of the benchmark 0.997-0.999), but the prediction's error is
+    high-frequency, which the first cycle removes anyway.  A predictor that saves iterations
+    fails this test, and the design notes that record the absence of a gain must then be
+    updated with it."""
     from paper_1604_07994_gb300 import guess
     X, T, gen = guess.training_set(64, n=16, seed=500, batch=32)
     assert gen["iterations_max"] < 400
@@ -215,5 +237,5 @@ def test_trained_guess_against_zero_start(sdx):
         z, g = e["zero"], e["guess_s4"]
         assert g["initial_rel_res"] <= 1.0 + 1e-12
         assert z["final_rel_res"] <= 1e-8 and g["final_rel_res"] <= 1e-8
-        print(e["name"], "iterations zero", z["iterations"], "guess", g["iterations"],
-              "initial error of the guess", g["initial_rel_error"])
+        assert abs(g["iterations"] - z["iterations"]) <= 1, (e["name"], z["iterations"], g["iterations"],
+                                                             g["initial_rel_res"])
