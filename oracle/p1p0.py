@@ -252,6 +252,91 @@ class P1P0:
         return np.array([l2, en, q])
 
 
+def _cell_tets(n, ci, cj, ck):
+    """The six Kuhn tetrahedra of cell (ci, cj, ck) as (oracle index, [4] node indices): the
+    path c, c + e_s1, c + e_s1 + e_s2, c + (1, 1, 1) for each axis permutation s of PERMS; the
+    index numbers tetrahedra permutation by permutation, cells i-major inside (kuhn_tets)."""
+    from .mesh import PERMS
+    n1 = n + 1
+    out = []
+    for si, s in enumerate(PERMS):
+        off = [0, 0, 0]
+        verts = [ci + n1 * (cj + n1 * ck)]
+        for ax in s:
+            off[ax] += 1
+            verts.append(ci + off[0] + n1 * (cj + off[1] + n1 * (ck + off[2])))
+        out.append((si * n ** 3 + (ci * n + cj) * n + ck, verts))
+    return out
+
+
+def _tet_geometry(n, verts):
+    """Barycentric gradients [4, 3] and volume of the tetrahedron with these node indices."""
+    n1 = n + 1
+    v = np.asarray(verts)
+    xyz = np.stack([v % n1, (v // n1) % n1, v // (n1 * n1)], axis=1) / n
+    M = np.concatenate([np.ones((4, 1)), xyz], axis=1)
+    return np.linalg.inv(M)[1:, :].T, abs(np.linalg.det(M)) / 6.0
+
+
+def sampled_rows_p1p0(n, cell_mu, face, form, u, p, nodes, tets, gamma: float = GAMMA):
+    """Rows of K x at selected velocity nodes and tetrahedra, for grids too large to assemble
+    (the full-size parity test).  Velocity rows: A u from oracle.forms.sampled_rows plus the
+    P0 gradient sum over the tetrahedra T around the node of -|T| grad lambda_b p_T; pressure
+    rows: (B0 u)_T = -|T| div u_h on T minus (C0 p)_T = sum over the facets F of T shared with a
+    tetrahedron T' of the same viscosity of gamma / (2 mu) |T||T'| / (|T| + |T'|) (p_T - p_T'),
+    the facet neighbours found by shared vertices among the tetrahedra of the 27 cells around
+    T's cell.  u: [3, (n+1)^3] (zero at constrained DoFs); p: [6 n^3] in the oracle's order;
+    nodes: node indices; tets: (permutation index, ci, cj, ck) tuples.  Returns ([3, len(nodes)]
+    velocity rows, constrained components zero; [len(tets)] pressure rows)."""
+    from .forms import sampled_rows, _BoundaryOnly
+    n1 = n + 1
+    nn = n1 ** 3
+    cell_mu = np.asarray(cell_mu, dtype=np.float64).ravel()
+    mu_cell = lambda ci, cj, ck: cell_mu[ci + n * (cj + n * ck)]  # noqa: E731
+    nodes = np.asarray(nodes)
+    x4 = np.concatenate([np.asarray(u, dtype=np.float64).reshape(3, nn), np.zeros((1, nn))])
+    vel = sampled_rows(n, cell_mu, face, form, x4.ravel(), nodes)[:3].copy()
+    for t, b in enumerate(nodes):
+        bi, bj, bk = b % n1, (b // n1) % n1, b // (n1 * n1)
+        for ck in (bk - 1, bk):
+            for cj in (bj - 1, bj):
+                for ci in (bi - 1, bi):
+                    if min(ci, cj, ck) < 0 or max(ci, cj, ck) >= n:
+                        continue
+                    for idx, verts in _cell_tets(n, ci, cj, ck):
+                        if b not in verts:
+                            continue
+                        grad, vol = _tet_geometry(n, verts)
+                        vel[:, t] += -vol * grad[verts.index(b)] * p[idx]
+    vel[_BoundaryOnly(n, face).constrained_nodes(nodes)] = 0.0
+    pre = np.zeros(len(tets))
+    for t, (si, ci, cj, ck) in enumerate(tets):
+        own = dict(_cell_tets(n, ci, cj, ck))
+        idx = si * n ** 3 + (ci * n + cj) * n + ck
+        verts = own[idx]
+        grad, vol = _tet_geometry(n, verts)
+        divu = sum(u[i][verts[a]] * grad[a, i] for a in range(4) for i in range(3))
+        row = -vol * divu
+        mu = mu_cell(ci, cj, ck)
+        vs = set(verts)
+        for dk in (-1, 0, 1):
+            for dj in (-1, 0, 1):
+                for di in (-1, 0, 1):
+                    cc = (ci + di, cj + dj, ck + dk)
+                    if min(cc) < 0 or max(cc) >= n:
+                        continue
+                    for idx2, v2 in _cell_tets(n, *cc):
+                        if idx2 == idx or len(vs.intersection(v2)) != 3:
+                            continue
+                        if mu_cell(*cc) != mu:
+                            continue  # a facet on the viscosity interface carries no penalty
+                        _, vol2 = _tet_geometry(n, v2)
+                        w = gamma / (2.0 * mu) * vol * vol2 / (vol + vol2)
+                        row -= w * (p[idx] - p[idx2])
+        pre[t] = row
+    return vel, pre
+
+
 def masked_p1p0(K: sp.spmatrix, con: np.ndarray) -> sp.csr_matrix:
     """The saddle matrix with constrained rows and columns replaced by identity rows."""
     return masked(K, con)

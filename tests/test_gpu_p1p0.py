@@ -198,3 +198,39 @@ def test_p0_couette_errors_match_oracle(sdx):
         x = to_oracle(_host(xd), n) + np.where(O.constrained(), xD, 0.0)
         x[3 * O.nn:] -= np.sum(O.vol * x[3 * O.nn:]) / O.vol.sum() - np.sum(O.vol * xo[3 * O.nn:]) / O.vol.sum()
         assert np.linalg.norm(x - xo) <= 1e-7 * np.linalg.norm(xo)
+
+
+@pytest.mark.parametrize("form", ["tr", "sym"])
+def test_p0_full_size_sampled_rows(sdx, form):
+    """128^3 cells, the columns problem of the benchmark's P1-P0 block (18.9M unknowns), one
+    apply on a random state: sampled velocity rows (nodes next to the free-slip faces, on the
+    columns' viscosity interfaces, in the interior, at ragged positions in x) and pressure rows
+    (all six tetrahedra of cells at the same places) against the oracle's locally assembled rows
+    (sampled_rows_p1p0) at 1e-13 of the largest sampled value."""
+    from oracle.forms import _BoundaryOnly
+    from oracle.p1p0 import sampled_rows_p1p0
+    p = W.viscosity_columns(128, 4)
+    n = p.n
+    H = sdx.P1P0(p, form=form)
+    _, nn, nT, _ = H.size(0)
+    rng = np.random.Generator(np.random.PCG64(29))
+    x = rng.uniform(-1, 1, 3 * nn + nT)
+    con = _BoundaryOnly(n, p.face).constrained_nodes(np.arange(nn))
+    x[: 3 * nn][con.ravel()] = 0.0
+    y = _dev(np.zeros_like(x))
+    H.apply(0, _dev(x), y)  # x is drawn in the library's order; the oracle reads it through _perm
+    yh = _host(y)
+    n1 = n + 1
+    picks = [(1, 1, 1), (1, 64, 64), (32, 32, 7), (31, 50, 9), (33, 96, 100), (96, 95, 127),
+             (127, 127, 126), (64, 1, 64), (5, 32, 33), (77, 96, 3), (126, 63, 64), (97, 97, 97)]
+    nodes = np.array([i + n1 * (j + n1 * k) for i, j, k in picks])
+    cells = [(min(i, n - 1), min(j, n - 1), min(k, n - 1)) for i, j, k in picks]
+    tets = [(s, ci, cj, ck) for ci, cj, ck in cells for s in range(6)]
+    p_oracle = x[3 * nn + _perm(n)]  # oracle order
+    vel, pre = sampled_rows_p1p0(n, p.cell_mu().ravel(), p.face, form, x[: 3 * nn].reshape(3, -1), p_oracle,
+                                 nodes, tets)
+    gv = yh[: 3 * nn].reshape(3, -1)[:, nodes]
+    gp = np.array([yh[3 * nn + s * n ** 3 + ci + n * (cj + n * ck)] for s, ci, cj, ck in tets])
+    scale = max(np.abs(vel).max(), np.abs(pre).max())
+    assert np.abs(gv - vel).max() <= 1e-13 * scale
+    assert np.abs(gp - pre).max() <= 1e-13 * scale

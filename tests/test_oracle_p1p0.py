@@ -163,3 +163,32 @@ def test_flux_balance_and_multigrid_solution():
     w[3 * L.nn:] = L.mp
     x[3 * L.nn:] -= np.dot(w, x) / L.mp.sum()
     assert np.linalg.norm(x - xd) <= 1e-8 * np.linalg.norm(xd)
+
+
+@pytest.mark.parametrize("form", ["tr", "sym"])
+def test_sampled_rows_equal_the_assembled_saddle_matrix(form):
+    """The locally assembled rows of sampled_rows_p1p0 (used at sizes too large to assemble)
+    equal the rows of the globally assembled saddle matrix [[A, B0^T], [B0, -C0]] (facets found
+    there by sorting vertex triples, here by a local search) on random states, constrained
+    velocity entries zero: every node's velocity rows and every ninth tetrahedron's pressure row
+    (all six permutations, interior, boundary and interface cells) at 1e-13."""
+    from oracle.p1p0 import sampled_rows_p1p0
+    for p in (W.viscosity_columns(8, 4), W.cube_inclusion(8, 4)):
+        n = p.n
+        O = P1P0(n, p.cell_mu().ravel(), p.face)
+        con = O.constrained()
+        rng = np.random.Generator(np.random.PCG64(17))
+        x = rng.uniform(-1, 1, 3 * O.nn + O.nT)
+        x[con] = 0.0
+        y = O.saddle(form) @ x
+        y[con] = 0.0
+        nodes = np.arange(O.nn)
+        T = np.arange(0, O.nT, 9)
+        s, r = np.divmod(T, n ** 3)
+        ci, r = np.divmod(r, n * n)
+        cj, ck = np.divmod(r, n)
+        vel, pre = sampled_rows_p1p0(n, p.cell_mu().ravel(), p.face, form, x[: 3 * O.nn].reshape(3, -1),
+                                     x[3 * O.nn:], nodes, list(zip(s, ci, cj, ck)))
+        scale = np.abs(y).max()
+        assert np.abs(vel.ravel() - y[: 3 * O.nn]).max() <= 1e-13 * scale
+        assert np.abs(pre - y[3 * O.nn + T]).max() <= 1e-13 * scale
