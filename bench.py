@@ -31,7 +31,7 @@ FP64_PEAK_FLOP_PER_CLK_PER_SM = 4  # 2 DFMA per clock per SM (GB300: 1.25 TFLOP/
 # from the ncu capture summarised in profiles/k_vel_uniform_three_boxes_128.md
 VEL_PASS_DRAM_BYTES_128 = 124941568 + 14626816
 # the same for the red FP64 pressure pass (profiles/k_pre_uniform_three_boxes_128.md)
-PRE_PASS_DRAM_BYTES_128 = 98797824 + 4326912
+PRE_PASS_DRAM_BYTES_128 = 98697984 + 4342016
 # the kernel of the benchmark's `roofline` object: the largest share of the step in the launch
 # list summarised in profiles/ (the pressure pass runs on every level)
 DOMINANT_KERNEL = "pressure_pass"

@@ -116,21 +116,22 @@ __device__ __forceinline__ bool interior_node(int n, int i, int j, int k) {
     return i > 0 && j > 0 && k > 0 && i < n && j < n && k < n;
 }
 
-// Sum over the seven Kuhn directions d of sum_i s_i(d) A_d(u_i), where s_i(d) = +1 if d has a
-// component along axis i and -1 otherwise: with it, B u = h^2 [T / 12 + (A_ex(u_x) + A_ey(u_y) +
-// A_ez(u_z)) / 6] (the B stencil of stencil.cuh, its e_i weight 1/4 split as 1/12 + 1/6).
+// B u = (h^2 / 12) [T + 2 (A_ex(u_x) + A_ey(u_y) + A_ez(u_z))] (the B stencil of stencil.cuh, its
+// e_i weight 1/4 split as 1/12 + 1/6), T the sum over the seven Kuhn directions d of
+// sum_i s_i(d) A_d(u_i) with s_i(d) = +1 if d has a component along axis i and -1 otherwise.
+// Returns the bracket; the three axis terms enter with weight 3 through FMAs (one pass over
+// the 21 differences, no separate diagonal sum).
 template <typename T>
-__device__ __forceinline__ void bu_sums(const T um[3][7], const T up[3][7], T& tsum, T& diag) {
+__device__ __forceinline__ T bu_sum(const T um[3][7], const T up[3][7]) {
     T A[3][7];
 #pragma unroll
     for (int c = 0; c < 3; ++c)
 #pragma unroll
         for (int d = 0; d < 7; ++d) A[c][d] = um[c][d] - up[c][d];
-    tsum = ((A[0][EX] - A[1][EX] - A[2][EX]) + (A[1][EY] - A[0][EY] - A[2][EY])) +
-           ((A[2][EZ] - A[0][EZ] - A[1][EZ]) + (A[0][EXY] + A[1][EXY] - A[2][EXY])) +
+    return ((fma(T(3), A[0][EX], -(A[1][EX] + A[2][EX])) + fma(T(3), A[1][EY], -(A[0][EY] + A[2][EY]))) +
+            (fma(T(3), A[2][EZ], -(A[0][EZ] + A[1][EZ])) + (A[0][EXY] + A[1][EXY] - A[2][EXY]))) +
            ((A[0][EXZ] + A[2][EXZ] - A[1][EXZ]) + (A[1][EYZ] + A[2][EYZ] - A[0][EYZ])) +
            (A[0][EXYZ] + A[1][EXYZ] + A[2][EXYZ]);
-    diag = A[0][EX] + A[1][EY] + A[2][EZ];
 }
 
 // The seven pressure differences A_d(p) and their combination D = sum of the four diagonal
@@ -186,12 +187,11 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
 #pragma unroll
             for (int d = 0; d < 7; ++d) { U[c].m[d] = um[c][d]; U[c].p[d] = up[c][d]; }
         }
+        T X[3];
+        cross_sums(U, X);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
-            T lap = T(8) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj);
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-                if (ii != jj) lap += xstencil(U[ii], ii, jj);
+            const T lap = T(8) * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj) + X[jj];
             row[jj] = fma(muh, lap, fma(-L.h2_3, A[jj], fma(L.h2_6, A[pair[jj]], btD)));
         }
     } else {
@@ -201,10 +201,8 @@ __device__ __forceinline__ void apply_uniform_node(const LevelView<T>& L, long l
             row[jj] = fma(muh, fma(T(6), uc[jj], -s), fma(-L.h2_3, A[jj], fma(L.h2_6, A[pair[jj]], btD)));
         }
     }
-    T tsum, dsum;
-    bu_sums(um, up, tsum, dsum);
     const T sp = ((pm[EX] + pp[EX]) + (pm[EY] + pp[EY])) + (pm[EZ] + pp[EZ]);
-    const T rowp = fma(L.h2_12, tsum, fma(L.h2_6, dsum, -tauh * fma(T(6), pc, -sp)));
+    const T rowp = fma(L.h2_12, bu_sum(um, up), -tauh * fma(T(6), pc, -sp));
 #pragma unroll
     for (int jj = 0; jj < 3; ++jj) y[jj * nn + node] = b ? bv[jj] - row[jj] : row[jj];
     y[3 * nn + node] = b ? bv[3] - rowp : rowp;
@@ -261,13 +259,12 @@ __device__ __forceinline__ void vel_uniform_node(const LevelView<T>& L, int i, i
         const T idA = L.idA[id], a1 = L.a1[id], a2 = L.a2[id], a3 = L.a3[id];
         T A[7];
         const T aD = a3 * bt_diffs(pm, pp, A);
+        T X[3];
+        cross_sums(U, X);
 #pragma unroll
         for (int jj = 0; jj < 3; ++jj) {
             // u_j = (S_xyz(u_j) + S_j(u_j) - sum_i X_ij(u_i)) / 8 + (f_j - (B^T p)_j) / (8 mu h)
-            T w = (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) + U[jj].S(jj);
-#pragma unroll
-            for (int ii = 0; ii < 3; ++ii)
-                if (ii != jj) w -= xstencil(U[ii], ii, jj);
+            const T w = (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) + U[jj].S(jj) - X[jj];
             out[jj * nn + node] = fma(w, T(0.125), fma(idA, fv[jj], fma(a1, A[jj], fma(a2, A[pair[jj]], aD))));
         }
     } else {
@@ -298,15 +295,13 @@ __device__ __forceinline__ void vel_copy_node(const LevelView<T>& L, int i, int 
     for (int c = 0; c < 3; ++c) x[c * L.nn + node] = ldx<LP>(src + c * L.nn + node);
 }
 
-// New pressure of a uniform node: (1 - omega) p + (omega / 6) S_p + k12 (2 diag + T)(u) - idC g,
-// with S_p the sum of the six axis neighbours of p and the B u sums of bu_sums over the 14 Kuhn
+// New pressure of a uniform node: (1 - omega) p + (omega / 6) S_p + k12 (T + 2 diag)(u) - idC g,
+// with S_p the sum of the six axis neighbours of p and the B u bracket of bu_sum over the 14 Kuhn
 // neighbours of the three velocity components (um / up: minus / plus).  Shared by every kernel
 // that updates these rows, so they agree to the bit.
 template <typename T>
 __device__ __forceinline__ T pre_update(const T um[3][7], const T up[3][7], T pc, T sp, T gv, T idC, T k12) {
-    T tsum, dsum;
-    bu_sums(um, up, tsum, dsum);
-    return fma(k12, fma(T(2), dsum, tsum), fma(-idC, gv, fma(T(OMEGA / 6.0), sp, T(1.0 - OMEGA) * pc)));
+    return fma(k12, bu_sum(um, up), fma(-idC, gv, fma(T(OMEGA / 6.0), sp, T(1.0 - OMEGA) * pc)));
 }
 
 // Pressure Gauss-Seidel on C p = B u - g with relaxation OMEGA at one non-special node:

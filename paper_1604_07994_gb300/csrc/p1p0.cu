@@ -102,10 +102,10 @@ __device__ __forceinline__ void au_row(const LevelView<double>& L, const double*
         if (FORM == FORM_SYM) {
             Nb15<double> U[3];
             for (int c = 0; c < 3; ++c) load_nb15(x + c * nn, node, L, U[c]);
+            double X[3];
+            cross_sums(U, X);
             for (int jj = 0; jj < 3; ++jj) {
-                double lap = 8.0 * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj);
-                for (int ii = 0; ii < 3; ++ii)
-                    if (ii != jj) lap += xstencil(U[ii], ii, jj);
+                const double lap = 8.0 * U[jj].c - (U[jj].S(EX) + U[jj].S(EY) + U[jj].S(EZ)) - U[jj].S(jj) + X[jj];
                 au[jj] = muh * lap;
                 idiag[jj] = L.idA[id];
             }

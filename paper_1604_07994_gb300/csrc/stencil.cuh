@@ -106,13 +106,29 @@ __device__ __forceinline__ int pair_dir(int i, int j) {
     return s == 1 ? EXY : (s == 2 ? EXZ : EYZ);
 }
 
-// Strain cross stencil X_ij applied to component values v (i != j), times 1 (units mu h)
+// Sums of the strain cross stencils into the three rows: X[j] = sum over i != j of X_ij(U_i),
+// in units of mu h, where for i != j and k the third axis
+//   X_ij(v) = (S_i + S_j - S_{e_i+e_j}) / 3 + (S_{e_i+e_k} + S_{e_j+e_k} - S_k - S_exyz) / 6 - 2 v(b) / 3.
+// For a fixed component i the stencils into its two other rows j, k share
+// Q_i = S_i / 3 + (S_{e_j+e_k} - S_exyz) / 6 - 2 c / 3; with a = S_j - S_{e_i+e_j} and
+// b = S_k - S_{e_i+e_k}, X_ij = Q_i + a / 3 - b / 6 and X_ik = Q_i + b / 3 - a / 6 (10 operations
+// per component instead of 14).
 template <typename T>
-__device__ __forceinline__ T xstencil(const Nb15<T>& v, int i, int j) {
-    const int k = 3 - i - j;
-    const int dij = pair_dir(i, j), dik = pair_dir(i, k), djk = pair_dir(j, k);
-    return T(1.0 / 3.0) * (v.S(i) + v.S(j) - v.S(dij)) +
-           T(1.0 / 6.0) * (v.S(dik) + v.S(djk) - v.S(k) - v.S(EXYZ)) - T(2.0 / 3.0) * v.c;
+__device__ __forceinline__ void cross_sums(const Nb15<T> U[3], T X[3]) {
+    T part[3][3];  // part[i][j] = X_ij(U_i)
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int j = (i + 1) % 3, k = (i + 2) % 3;
+        const T Q = fma(T(1.0 / 3.0), U[i].S(i),
+                        fma(T(1.0 / 6.0), U[i].S(pair_dir(j, k)) - U[i].S(EXYZ), T(-2.0 / 3.0) * U[i].c));
+        const T a = U[i].S(j) - U[i].S(pair_dir(i, j));
+        const T b = U[i].S(k) - U[i].S(pair_dir(i, k));
+        part[i][j] = fma(T(1.0 / 3.0), a, fma(T(-1.0 / 6.0), b, Q));
+        part[i][k] = fma(T(1.0 / 3.0), b, fma(T(-1.0 / 6.0), a, Q));
+    }
+    X[0] = part[1][0] + part[2][0];
+    X[1] = part[0][1] + part[2][1];
+    X[2] = part[0][2] + part[1][2];
 }
 
 // ------------------------------------------------------------------ general evaluation
