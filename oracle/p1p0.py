@@ -442,7 +442,11 @@ class P1P0Hierarchy:
     """Levels n, n/2, ..., n_coarse of the P1-P0 scheme with rediscretised operators, V_var
     cycle with nu = 3 + 2k Uzawa steps k levels below the finest, direct coarsest solve."""
 
-    def __init__(self, n, n_coarse, cell_mu, face, form="tr", coarse_form=None, gamma=GAMMA):
+    def __init__(self, n, n_coarse, cell_mu, face, form="tr", coarse_form=None, gamma=GAMMA,
+                 coarsening="resolved"):
+        """coarsening: how coarse cells take their viscosity ("resolved": the interfaces must be
+        resolved by every coarse grid; "majority": the majority rule of
+        oracle.solvers.coarsen_cell_mu for interfaces the coarse grids do not resolve)."""
         from .solvers import coarsen_cell_mu
         from .transfer import prolongation
         self.levels, self.P = [], []
@@ -453,7 +457,7 @@ class P1P0Hierarchy:
             self.levels.append(P1P0Level(m, mu, face, f, gamma))
             if m == n_coarse:
                 break
-            mu = coarsen_cell_mu(m, mu)
+            mu = coarsen_cell_mu(m, mu, coarsening)
             m //= 2
         for l in range(len(self.levels) - 1):
             fL, cL = self.levels[l], self.levels[l + 1]
