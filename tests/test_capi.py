@@ -117,3 +117,40 @@ def test_batch_validation_without_a_device():
     assert h.value is None
     assert lib.sdx_batch_destroy(None) == sdx.OK
     assert lib.sdx_batch_solve(None, None, None, 1e-8, 10, 10, None, None) == sdx.EINVAL
+
+
+def test_p1p0_argument_validation_without_a_device():
+    """The P1-P0 entry points reject bad arguments on the host, before any CUDA call: a
+    non-positive or non-finite penalty gamma, a null descriptor, FP32 cycles (the scheme runs in
+    FP64), the P1-P1 coarse-grid correction, the descriptor's own host checks, null handles
+    and vectors."""
+    from paper_1604_07994_gb300 import sdx
+    lib = ensure_built()
+    h = ctypes.c_void_p()
+    cells = np.zeros(8 ** 3, dtype=np.uint8)
+    mu = np.array([1.0])
+    d = sdx.sdx_desc()
+    d.n, d.n_coarse, d.n_mu = 8, 4, 1
+    d.cell_id = cells.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))
+    d.mu = mu.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    d.form, d.coarse_form, d.prec, d.pspg_beta = 0, -1, 0, sdx.PSPG_BETA
+    d.coarsest_form = -1
+    for gamma in (0.0, -1.0, float("nan"), float("inf")):
+        assert lib.sdx_p0_create(ctypes.byref(d), ctypes.c_double(gamma), ctypes.byref(h)) == sdx.EINVAL
+        assert b"gamma" in lib.sdx_last_error()
+    assert lib.sdx_p0_create(None, ctypes.c_double(1.0), ctypes.byref(h)) == sdx.EINVAL
+    assert lib.sdx_p0_create(ctypes.byref(d), ctypes.c_double(1.0), None) == sdx.EINVAL
+    d.prec = 1
+    assert lib.sdx_p0_create(ctypes.byref(d), ctypes.c_double(1.0), ctypes.byref(h)) == sdx.EINVAL
+    assert b"FP64" in lib.sdx_last_error()
+    d.prec, d.coarse_correction = 0, 1
+    assert lib.sdx_p0_create(ctypes.byref(d), ctypes.c_double(1.0), ctypes.byref(h)) == sdx.EINVAL
+    assert b"coarse_correction" in lib.sdx_last_error()
+    d.coarse_correction, d.n_coarse = 0, 3  # 8 is not 3 * 2^k
+    assert lib.sdx_p0_create(ctypes.byref(d), ctypes.c_double(1.0), ctypes.byref(h)) == sdx.EINVAL
+    assert b"n_coarse" in lib.sdx_last_error()
+    assert h.value is None
+    assert lib.sdx_p0_apply(None, 0, None, None, None) == sdx.EINVAL
+    assert lib.sdx_p0_solve(None, None, None, ctypes.c_double(1e-8), 10, 1, 30, None, None) == sdx.EINVAL
+    assert lib.sdx_p0_fluxes(None, None, None, None, None) == sdx.EINVAL
+    assert lib.sdx_p0_destroy(None) == sdx.OK
