@@ -228,3 +228,73 @@ def test_fp32_uzawa_steps_match_oracle(sdx, name, form, coarse_form, level, step
         assert launches == 1  # the single-cluster path
     else:
         assert launches >= 5 * steps
+
+
+def test_full_size_smoother_passes_sampled_rows(sdx):
+    """The benchmark's passes at the benchmark's size (128^3 three boxes, mu ratio 1e4, decoupled
+    form, FP64): one red velocity pass and one red pressure pass from a random state, checked at
+    sampled nodes (interface rows, rows next to the walls, uniform interior rows, both colours)
+    against the oracle's locally assembled rows (oracle.forms.sampled_rows): a red node takes
+    u + (f - A u - B^T p) / diag(A) on its free components and p + omega (B u - C p - g) /
+    diag(C) respectively, with the diagonals probed by unit vectors; black nodes keep their values
+    to the bit.  1e-13 of the largest sampled value."""
+    from oracle.forms import sampled_rows
+    p = W.three_boxes(128, 8, contrast=1e4)
+    n = p.n
+    n1 = n + 1
+    nn = n1 ** 3
+    cm = p.cell_mu().ravel()
+    H = sdx.Hierarchy.from_problem(p, form="tr", coarse_form="sym", prec=sdx.PREC_FP64)
+    con = H.sdx_constraint_mask(0)
+    iface = np.flatnonzero(H.sdx_interface_mask(0))
+    rng = np.random.Generator(np.random.PCG64(93))
+    x = W.random_vector(n, 91).ravel()
+    b = W.random_vector(n, 92).ravel()
+    x[con] = 0.0
+    b[con] = 0.0
+    picks = [(1, 1, 1), (2, 1, 1), (64, 64, 64), (65, 64, 64), (127, 126, 127), (126, 127, 127), (1, 77, 33)]
+    nodes = [i + n1 * (j + n1 * k) for i, j, k in picks]
+    nodes += list(rng.choice(iface, 8, replace=False)) + list(rng.integers(0, nn, 6))
+    nodes = np.array(sorted(set(int(v) for v in nodes)))
+    ijk = np.stack([nodes % n1, (nodes // n1) % n1, nodes // (n1 * n1)])
+    red = (ijk.sum(axis=0) % 2) == 0
+    assert red.any() and (~red).any() and np.isin(iface, nodes).any()
+    rows = sampled_rows(n, cm, p.face, "tr", x, nodes)  # [4, len(nodes)]: A u + B^T p ; B u - C p
+    diagA = np.zeros((3, len(nodes)))
+    diagC = np.zeros(len(nodes))
+    for t, v in enumerate(nodes):
+        for c in range(4):
+            e = np.zeros(4 * nn)
+            if c < 3 and con[c * nn + v]:
+                continue
+            e[c * nn + v] = 1.0
+            r = sampled_rows(n, cm, p.face, "tr", e, np.array([v]))[:, 0]
+            if c < 3:
+                diagA[c, t] = r[c]
+            else:
+                diagC[t] = -r[3]
+    # velocity pass, colour 0
+    xd = _dev(x)
+    H.sdx_smooth_pass(0, 0, 0, _dev(b), xd)
+    xg = _host(xd)
+    for t, v in enumerate(nodes):
+        for c in range(3):
+            old = x[c * nn + v]
+            got = xg[c * nn + v]
+            if not red[t] or con[c * nn + v]:
+                assert got == old, (v, c)
+            else:
+                want = old + (b[c * nn + v] - rows[c, t]) / diagA[c, t]
+                assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (v, c, got, want)
+    # pressure pass, colour 0, from the same state
+    xd = _dev(x)
+    H.sdx_smooth_pass(0, 1, 0, _dev(b), xd)
+    xg = _host(xd)
+    for t, v in enumerate(nodes):
+        old = x[3 * nn + v]
+        got = xg[3 * nn + v]
+        if not red[t]:
+            assert got == old, v
+        else:
+            want = old + OMEGA * (rows[3, t] - b[3 * nn + v]) / diagC[t]
+            assert abs(got - want) <= 1e-13 * max(1.0, abs(want)), (v, got, want)
