@@ -494,10 +494,11 @@ def run_batch(args, sdx, torch, count=None):
     t0 = time.perf_counter()
     B = sdx.Batch(probs, prec=sdx.PREC_FP32_REFINED, coarse_form="sym", autotune=True)
     setup = time.perf_counter() - t0
-    bs, xs, free = [], [], 0
+    bs, xs, free, sizes = [], [], 0, []
     for i, p in enumerate(probs):
         H = B.instance(i)
         free += H.sdx_level_size(0)[2]
+        sizes.append([H.sdx_level_size(l)[1:] for l in range(H.sdx_levels())])  # (nodes, free) per level
         f = torch.from_numpy(p.nodal_forcing().ravel()).cuda()
         b = torch.zeros(4 * p.nodes, dtype=torch.float64, device="cuda")
         H.sdx_rhs(f, b)
@@ -541,7 +542,27 @@ def run_batch(args, sdx, torch, count=None):
         its_seq.append(s1["iterations"])
         H.close()
     B.close()
+    # algorithmic bytes of the solves (a lower bound of their traffic): per FGMRES iteration one
+    # FP32 V_var(3,3) cycle (per level l with N_l nodes: 2 nu_l Uzawa steps of 3 velocity passes
+    # x 30 B and 2 pressure passes x 24 B per node, the residual 34 B, restriction 16 + 16 and
+    # prolongation 16 + 32 B per fine / coarse node; the coarsest dense FP64 mat-vec) and one FP64
+    # operator apply (64 B per node); Krylov vectors and the FP64/FP32 conversions not counted
+    pk = peaks().get("hbm_gbs")
+    total = 0.0
+    for lv, it in zip(sizes, its):
+        ns = [nodes for nodes, _ in lv]
+        cyc = 0.0
+        for l, N in enumerate(ns[:-1]):
+            nu = 3 + 2 * l
+            cyc += N * (2 * nu * (3 * 30 + 2 * 24) + 34 + 16 + 32) + ns[l + 1] * (16 + 16)
+        cyc += 8.0 * float(lv[-1][1]) ** 2  # the coarsest inverse over its free unknowns
+        total += it * (cyc + 64.0 * ns[0])
+    hbm = {"algorithmic_gbs_lower_bound": total / tb / 1e9,
+           "frac_of_measured_hbm": total / tb / 1e9 / pk if pk else None,
+           "lockstep_frac_of_measured_hbm": total / t_lock / 1e9 / pk if pk else None,
+           "counted": "per FGMRES iteration: the FP32 V-cycle's passes, residuals and transfers on every level, the coarsest mat-vec, one FP64 apply; Krylov vectors and conversions not counted"}
     return {"workload": f"{count} instances, sizes {sorted(set(p.n for p in probs))}^3 cells, 1-4 boxes, contrast log-uniform in [1, 1e6], Gaussian-blob forcing",
+            "hbm_roofline": hbm,
             "total_free_dofs": int(free), "time_to_1e8_s": tb, "gdofs": free / tb / 1e9, "all_converged": all(s["status"] == 0 for s in st),
             "iterations_mean": float(np.mean(its)), "iterations_max": int(max(its)), "setup_s": setup,
             "gpu_launches_per_solve": int(launches), "block_shapes_per_level": shapes,
@@ -1031,6 +1052,19 @@ def run_p1p0(args, sdx, torch, levels=(0, 1, 2, 3, 4, 5)):
     flux = torch.empty(4 * tets, dtype=torch.float64, device="cuda")
     bal = torch.empty(tets, dtype=torch.float64, device="cuda")
     H.fluxes(x, flux, bal)
+    # the operator apply against both roofs: algorithmic bytes = x read and y written once
+    # (8 B per unknown each) plus the node info and cell ids (3 B per node); algorithmic flops =
+    # 75 per node (7-point Laplacians 3 x 8, the P0 gradient over the 24 tetrahedra around the
+    # node 48, scaling 3) + 14 per tetrahedron (divergence 6, four penalised facets 8)
+    y = torch.empty_like(x)
+    t_ap = _time(lambda: H.apply(0, x, y), 20, torch.cuda.current_stream(), torch)
+    by = 16.0 * (3 * nodes + tets) + 3.0 * nodes
+    fl = 75.0 * nodes + 14.0 * tets
+    pk = peaks().get("hbm_gbs")
+    fp64_peak = N_SM * FP64_PEAK_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
+    gbs, tfl = by / (t_ap * 1e-3) / 1e9, fl / (t_ap * 1e-3) / 1e12
+    out["apply_128"] = {"ms": t_ap, "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / pk if pk else None,
+                        "algorithmic_tflops": tfl, "frac_of_fp64_peak": tfl / fp64_peak}
     out["columns"] = {"cells": nc, "free_dofs": free, "time_to_1e8_s": ts, "gdofs": free / ts / 1e9,
                       "iterations": st["iterations"],
                       "max_element_imbalance_over_max_flux": float(bal.abs().max() / flux.abs().max())}

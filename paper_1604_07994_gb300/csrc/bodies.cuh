@@ -20,11 +20,16 @@ __device__ __constant__ int KUHN14[14][3] = {
     {-1, -1, 0}, {1, 0, 1}, {-1, 0, -1}, {0, 1, 1}, {0, -1, -1}, {1, 1, 1}, {-1, -1, -1}};
 }  // namespace
 
+// Every level has fewer than 2^32 nodes (n <= 1024, checked at creation), so the index is split
+// with unsigned 32-bit divisions: a 64-bit division by a runtime divisor is a long instruction
+// sequence, and the colour passes are issue-bound.
 __device__ __forceinline__ void node_ijk(long long b, int n1, int& i, int& j, int& k) {
-    i = (int)(b % n1);
-    long long t = b / n1;
-    j = (int)(t % n1);
-    k = (int)(t / n1);
+    const unsigned u = (unsigned)b, m = (unsigned)n1;
+    const unsigned t = u / m;
+    i = (int)(u - t * m);
+    const unsigned kk = t / m;
+    j = (int)(t - kk * m);
+    k = (int)kk;
 }
 
 // Viscosity id of a uniform node: any of its eight cells, here the one with origin
@@ -36,13 +41,15 @@ __device__ __forceinline__ int uniform_id(const LevelView<T>& L, int i, int j, i
 
 // Dense numbering of the nodes of one colour: rows (j, k) of half = (n1+1)/2 slots, slot s of
 // a row is node i = 2s + ((colour + j + k) & 1).  Returns false for slots past the grid.
+// (Slot numbers stay below 2^32 like node numbers: unsigned 32-bit divisions.)
 __device__ __forceinline__ bool colour_slot(int n1, int colour, long long t, int& i, int& j,
                                             int& k) {
-    const int half = (n1 + 1) >> 1;
-    const long long row = t / half;
-    const int slot = (int)(t - row * half);
-    j = (int)(row % n1);
-    k = (int)(row / n1);
+    const unsigned half = (unsigned)(n1 + 1) >> 1, m = (unsigned)n1, u = (unsigned)t;
+    const unsigned row = u / half;
+    const int slot = (int)(u - row * half);
+    const unsigned kk = row / m;
+    j = (int)(row - kk * m);
+    k = (int)kk;
     i = 2 * slot + ((colour + j + k) & 1);
     return k < n1 && i < n1;
 }

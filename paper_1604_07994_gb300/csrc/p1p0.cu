@@ -177,6 +177,25 @@ namespace {
 
 constexpr int PTPB = 256;
 inline unsigned pblocks(long long count) { return (unsigned)((count + PTPB - 1) / PTPB); }
+// Launch shape of the per-tetrahedron kernels: blockIdx.y is the permutation s, x runs over the
+// n^3 cells (fewer than 2^32, so the cell is split with 32-bit divisions).
+inline dim3 tet_grid(int n) { return dim3(pblocks((long long)n * n * n), 6); }
+
+// Tetrahedron of this thread (tet_grid launch): permutation s, cell (i, j, k) and its index
+// t = s n^3 + i + n (j + n k); false past the last cell.
+__device__ __forceinline__ bool tet_of_thread(int n, int& s, int& i, int& j, int& k, long long& t) {
+    const unsigned m = (unsigned)n;
+    const unsigned cell = blockIdx.x * blockDim.x + threadIdx.x;
+    if (cell >= m * m * m) return false;
+    s = (int)blockIdx.y;
+    const unsigned r = cell / m;
+    i = (int)(cell - r * m);
+    const unsigned kk = r / m;
+    j = (int)(r - kk * m);
+    k = (int)kk;
+    t = (long long)s * ((long long)n * n * n) + cell;
+    return true;
+}
 
 // Velocity rows of every node.  MODE 0: y_u = A u + B^T p (b == nullptr) or b_u - (A u + B^T p);
 // MODE 1: velocity Gauss-Seidel of one colour staged: y_u = u + (f - A u - B^T p) / diag(A) at the
@@ -229,12 +248,9 @@ template <int MODE>
 __global__ void k_pre_rows(LevelView<double> L, double gamma, const double* __restrict__ x,
                            double* __restrict__ y, const double* __restrict__ b) {
     pdl_prologue();
-    const long long n3 = (long long)L.n * L.n * L.n;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 6 * n3) return;
-    const int s = (int)(t / n3);
-    const long long cell = t - s * n3;
-    const int i = (int)(cell % L.n), j = (int)((cell / L.n) % L.n), k = (int)(cell / ((long long)L.n * L.n));
+    int s, i, j, k;
+    long long t;
+    if (!tet_of_thread(L.n, s, i, j, k, t)) return;
     double mass;
     const double row = prow0(L, gamma, x, s, i, j, k, mass);
     const long long o = 3 * L.nn;
@@ -361,12 +377,10 @@ __global__ void k_p0_mv(const double* __restrict__ M, int n, const double* __res
 __global__ void k_p0_fluxes(LevelView<double> L, double gamma, const double* __restrict__ x,
                             double* __restrict__ flux, double* __restrict__ balance) {
     pdl_prologue();
+    int s, i, j, k;
+    long long t;
+    if (!tet_of_thread(L.n, s, i, j, k, t)) return;
     const long long n3 = (long long)L.n * L.n * L.n;
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= 6 * n3) return;
-    const int s = (int)(t / n3);
-    const long long cell = t - s * n3;
-    const int i = (int)(cell % L.n), j = (int)((cell / L.n) % L.n), k = (int)(cell / ((long long)L.n * L.n));
     const int n = L.n;
     const long long nn = L.nn;
     int a[3];
@@ -453,7 +467,7 @@ static void apply(P0Handle& Q, int l, const double* x, double* y, const double* 
     vel_rows(P, l, 0, 0, x, y, b, Q.maps.cfg_of[l], s);
     const LevelView<double> V = view<double>(*P.H, l);
     count_launches(1);
-    launch_k(k_pre_rows<0>, dim3(pblocks(P.lv[l].nT)), dim3(PTPB), s, V, P.gamma, x, y, b);
+    launch_k(k_pre_rows<0>, tet_grid(P.H->lv[l].n), dim3(PTPB), s, V, P.gamma, x, y, b);
 }
 
 static void uzawa(P0Handle& Q, int l, double* x, const double* b, cudaStream_t s) {
@@ -466,7 +480,7 @@ static void uzawa(P0Handle& Q, int l, double* x, const double* b, cudaStream_t s
         launch_k(k_vel_copy, dim3(pblocks(PL.nn)), dim3(PTPB), s, V, c, (const double*)PL.utmp, x);
     }
     count_launches(2);
-    launch_k(k_pre_rows<2>, dim3(pblocks(PL.nT)), dim3(PTPB), s, V, P.gamma, (const double*)x, PL.ptmp, b);
+    launch_k(k_pre_rows<2>, tet_grid(P.H->lv[l].n), dim3(PTPB), s, V, P.gamma, (const double*)x, PL.ptmp, b);
     launch_k(k_copy_n, dim3(pblocks(PL.nT)), dim3(PTPB), s, x + 3 * PL.nn, (const double*)PL.ptmp, PL.nT);
 }
 
@@ -936,7 +950,7 @@ int sdx_p0_fluxes(sdx_p0_t h, const double* x, double* flux, double* balance, vo
     if (!Q || !x || !flux || !balance) { set_error("null argument"); return SDX_EINVAL; }
     API_BEGIN
     count_launches(1);
-    launch_k(p0::k_p0_fluxes, dim3(p0::pblocks(Q->P.lv[0].nT)), dim3(p0::PTPB), (cudaStream_t)stream,
+    launch_k(p0::k_p0_fluxes, p0::tet_grid(Q->P.H->lv[0].n), dim3(p0::PTPB), (cudaStream_t)stream,
              view<double>(*Q->P.H, 0), Q->P.gamma, x, flux, balance);
     return launched("sdx_p0_fluxes");
     API_END
