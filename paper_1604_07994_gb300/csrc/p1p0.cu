@@ -44,6 +44,10 @@ struct P0Level {
     double* x = nullptr; double* b = nullptr; double* r = nullptr;
     double* utmp = nullptr;               // staged velocities of a colour (3 nn)
     double* ptmp = nullptr;               // Jacobi pressures (nT)
+    // per viscosity id: the facet weight gamma h^3 / (24 mu) and the inverse P0 mass 6 mu / h^3
+    // (tables, so that no kernel divides in FP64)
+    double* wt = nullptr;
+    double* imass = nullptr;
 };
 
 struct P0Hier {
@@ -85,7 +89,7 @@ __device__ __forceinline__ void btp0(const LevelView<double>& L, const double* _
         else if (m == 2) { out[a1] -= pt; out[a2] += pt; }
         else out[a2] -= pt;
     }
-    const double c = L.h * L.h / 6.0;
+    const double c = L.h2_6;
     out[0] *= c; out[1] *= c; out[2] *= c;
 }
 
@@ -134,9 +138,10 @@ __device__ __forceinline__ void au_row(const LevelView<double>& L, const double*
     }
 }
 
-// (B u)_T - (C p)_T of tetrahedron (s, cell (i, j, k)), and |T| / mu_T.
-__device__ __forceinline__ double prow0(const LevelView<double>& L, double gamma, const double* __restrict__ x,
-                                        int s, int i, int j, int k, double& mass) {
+// (B u)_T - (C p)_T of tetrahedron (s, cell (i, j, k)), and its viscosity id; wt: the facet
+// weight per id.
+__device__ __forceinline__ double prow0(const LevelView<double>& L, const double* __restrict__ wt,
+                                        const double* __restrict__ x, int s, int i, int j, int k, int& id) {
     const int n = L.n;
     const long long n3 = (long long)n * n * n, nn = L.nn;
     int a[3];
@@ -149,9 +154,8 @@ __device__ __forceinline__ double prow0(const LevelView<double>& L, double gamma
         hdiv += u[v + st[a[l]]] - u[v];
         v += st[a[l]];
     }
-    const double h = L.h;
-    const double bu = -(h * h / 6.0) * hdiv;
-    const int id = L.cid[(i + 1) + (long long)L.P * ((j + 1) + (long long)L.P * (k + 1))];
+    const double bu = -L.h2_6 * hdiv;
+    id = L.cid[(i + 1) + (long long)L.P * ((j + 1) + (long long)L.P * (k + 1))];
     const double mu = L.mu[id];
     const double* p = x + 3 * nn;
     const double pt = p[s * n3 + cell_of(n, i, j, k)];
@@ -162,14 +166,13 @@ __device__ __forceinline__ double prow0(const LevelView<double>& L, double gamma
     const int ns[4] = {perm_index(a[1], a[0], a[2]), perm_index(a[0], a[2], a[1]), perm_index(a[1], a[2], a[0]),
                        perm_index(a[2], a[0], a[1])};
     double cp = 0.0;
-    const double w = gamma * h * h * h / (24.0 * mu);
+    const double w = wt[id];
     for (int f = 0; f < 4; ++f) {
         if (ni[f] < 0 || nj[f] < 0 || nk[f] < 0 || ni[f] >= n || nj[f] >= n || nk[f] >= n) continue;
         const int idf = L.cid[(ni[f] + 1) + (long long)L.P * ((nj[f] + 1) + (long long)L.P * (nk[f] + 1))];
         if (L.mu[idf] != mu) continue;  // a facet on the viscosity interface is not penalised
         cp += w * (pt - p[ns[f] * n3 + cell_of(n, ni[f], nj[f], nk[f])]);
     }
-    mass = h * h * h / (6.0 * mu);
     return bu - cp;
 }
 
@@ -243,19 +246,20 @@ __global__ void k_vel_copy(LevelView<double> L, int colour, const double* __rest
 }
 
 // Pressure rows of every tetrahedron.  MODE 0: y_p = B u - C p (b == nullptr) or b_p - (B u - C p);
-// MODE 2: relaxed Jacobi step y_p = p + omega_p (mu_T / |T|) (B u - C p - g).
+// MODE 2: relaxed Jacobi step y_p = p + omega_p (mu_T / |T|) (B u - C p - g), mu_T / |T| from the
+// level's table.
 template <int MODE>
-__global__ void k_pre_rows(LevelView<double> L, double gamma, const double* __restrict__ x,
-                           double* __restrict__ y, const double* __restrict__ b) {
+__global__ void k_pre_rows(LevelView<double> L, const double* __restrict__ wt, const double* __restrict__ imass,
+                           const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ b) {
     pdl_prologue();
     int s, i, j, k;
     long long t;
     if (!tet_of_thread(L.n, s, i, j, k, t)) return;
-    double mass;
-    const double row = prow0(L, gamma, x, s, i, j, k, mass);
+    int id;
+    const double row = prow0(L, wt, x, s, i, j, k, id);
     const long long o = 3 * L.nn;
     if (MODE == 0) y[o + t] = b ? b[o + t] - row : row;
-    else y[t] = x[o + t] + OMEGA_P * (row - b[o + t]) / mass;
+    else y[t] = x[o + t] + OMEGA_P * (row - b[o + t]) * imass[id];
 }
 
 __global__ void k_copy_n(double* __restrict__ y, const double* __restrict__ x, long long count) {
@@ -374,7 +378,7 @@ __global__ void k_p0_mv(const double* __restrict__ M, int n, const double* __res
 // Post-processed fluxes of the four facets of every tetrahedron (outward) and their sum:
 // flux[4 t + f] = int_F u_h . n_T + w (p_T - p_F) (the penalty part only on facets inside one
 // viscosity; facets on the domain boundary carry u_h . n only).
-__global__ void k_p0_fluxes(LevelView<double> L, double gamma, const double* __restrict__ x,
+__global__ void k_p0_fluxes(LevelView<double> L, const double* __restrict__ wt, const double* __restrict__ x,
                             double* __restrict__ flux, double* __restrict__ balance) {
     pdl_prologue();
     int s, i, j, k;
@@ -394,7 +398,7 @@ __global__ void k_p0_fluxes(LevelView<double> L, double gamma, const double* __r
     const double mu = L.mu[id];
     const double* p = x + 3 * nn;
     const double pt = p[t];
-    const double w = gamma * h * h * h / (24.0 * mu);
+    const double w = wt[id];
     // facet opposite path vertex m: area-weighted outward normal |F| n = -|T| grad lambda_m * 3 =
     // -(h^2 / 2) g_m; flux of the P1 field = |F| n . (mean of the three facet vertices' u)
     const int fm_i[4] = {i + (a[0] == 0), i, i, i - (a[2] == 0)};
@@ -412,8 +416,9 @@ __global__ void k_p0_fluxes(LevelView<double> L, double gamma, const double* __r
         double um[3] = {0, 0, 0};
         for (int q = 0; q < 4; ++q) {
             if (q == m) continue;
-            for (int c = 0; c < 3; ++c) um[c] += x[c * nn + v[q]] / 3.0;
+            for (int c = 0; c < 3; ++c) um[c] += x[c * nn + v[q]];
         }
+        for (int c = 0; c < 3; ++c) um[c] *= 1.0 / 3.0;
         double f = -(h * h / 2.0) * (g[0] * um[0] + g[1] * um[1] + g[2] * um[2]);
         const int ni = fm_i[m], nj = fm_j[m], nk = fm_k[m];
         if (ni >= 0 && nj >= 0 && nk >= 0 && ni < n && nj < n && nk < n) {
@@ -467,7 +472,8 @@ static void apply(P0Handle& Q, int l, const double* x, double* y, const double* 
     vel_rows(P, l, 0, 0, x, y, b, Q.maps.cfg_of[l], s);
     const LevelView<double> V = view<double>(*P.H, l);
     count_launches(1);
-    launch_k(k_pre_rows<0>, tet_grid(P.H->lv[l].n), dim3(PTPB), s, V, P.gamma, x, y, b);
+    launch_k(k_pre_rows<0>, tet_grid(P.H->lv[l].n), dim3(PTPB), s, V, (const double*)P.lv[l].wt,
+             (const double*)P.lv[l].imass, x, y, b);
 }
 
 static void uzawa(P0Handle& Q, int l, double* x, const double* b, cudaStream_t s) {
@@ -480,7 +486,8 @@ static void uzawa(P0Handle& Q, int l, double* x, const double* b, cudaStream_t s
         launch_k(k_vel_copy, dim3(pblocks(PL.nn)), dim3(PTPB), s, V, c, (const double*)PL.utmp, x);
     }
     count_launches(2);
-    launch_k(k_pre_rows<2>, tet_grid(P.H->lv[l].n), dim3(PTPB), s, V, P.gamma, (const double*)x, PL.ptmp, b);
+    launch_k(k_pre_rows<2>, tet_grid(P.H->lv[l].n), dim3(PTPB), s, V, (const double*)PL.wt, (const double*)PL.imass,
+             (const double*)x, PL.ptmp, b);
     launch_k(k_copy_n, dim3(pblocks(PL.nT)), dim3(PTPB), s, x + 3 * PL.nn, (const double*)PL.ptmp, PL.nT);
 }
 
@@ -547,7 +554,7 @@ static void free_handle(P0Handle* Q) {
     if (!Q) return;
     cudaDeviceSynchronize();
     for (P0Level& L : Q->P.lv) {
-        void* p[] = {L.x, L.b, L.r, L.utmp, L.ptmp};
+        void* p[] = {L.x, L.b, L.r, L.utmp, L.ptmp, L.wt, L.imass};
         for (void* q : p) if (q) cudaFree(q);
     }
     for (int* m : Q->maps.cfg_of) if (m) cudaFree(m);
@@ -718,6 +725,20 @@ static P0Handle* create(const sdx_desc* d, double gamma) {
             B.r = dalloc<double>(B.len);
             B.utmp = dalloc<double>(3 * B.nn);
             B.ptmp = dalloc<double>(B.nT);
+            {
+                const double h = view<double>(*Q->P.H, (int)Q->P.lv.size() - 1).h;
+                std::vector<double> wt(256, 0.0), im(256, 0.0);
+                for (int id = 0; id < 256; ++id) {
+                    const double mu = Q->P.H->mu_table[id];
+                    if (!(mu > 0)) continue;  // the ghost id outside the domain
+                    wt[id] = gamma * h * h * h / (24.0 * mu);
+                    im[id] = 6.0 * mu / (h * h * h);
+                }
+                B.wt = dalloc<double>(256);
+                B.imass = dalloc<double>(256);
+                CK(cudaMemcpy(B.wt, wt.data(), sizeof(double) * 256, cudaMemcpyHostToDevice));
+                CK(cudaMemcpy(B.imass, im.data(), sizeof(double) * 256, cudaMemcpyHostToDevice));
+            }
             CK(cudaMemset(B.x, 0, sizeof(double) * B.len));
             Q->maps.cfg_of.push_back(node_configs(L));
         }
@@ -951,7 +972,7 @@ int sdx_p0_fluxes(sdx_p0_t h, const double* x, double* flux, double* balance, vo
     API_BEGIN
     count_launches(1);
     launch_k(p0::k_p0_fluxes, p0::tet_grid(Q->P.H->lv[0].n), dim3(p0::PTPB), (cudaStream_t)stream,
-             view<double>(*Q->P.H, 0), Q->P.gamma, x, flux, balance);
+             view<double>(*Q->P.H, 0), (const double*)Q->P.lv[0].wt, x, flux, balance);
     return launched("sdx_p0_fluxes");
     API_END
 }
