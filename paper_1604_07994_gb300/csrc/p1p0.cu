@@ -76,8 +76,15 @@ __device__ __forceinline__ void btp0(const LevelView<double>& L, const double* _
     const int n = L.n;
     const long long n3 = (long long)n * n * n;
     out[0] = out[1] = out[2] = 0.0;
+    // TET24 of stencil.cuh as a compile-time table: with the loop unrolled, every cell offset,
+    // permutation and path position below is a constant (same order of the adds as a loop)
+    constexpr signed char tab[24][3] = {
+        {0, 0, 0}, {0, 1, 0}, {0, 2, 0}, {0, 3, 0}, {0, 4, 0}, {0, 5, 0}, {1, 0, 1}, {1, 1, 1},
+        {2, 2, 1}, {2, 3, 1}, {3, 0, 2}, {3, 2, 2}, {4, 4, 1}, {4, 5, 1}, {5, 1, 2}, {5, 4, 2},
+        {6, 3, 2}, {6, 5, 2}, {7, 0, 3}, {7, 1, 3}, {7, 2, 3}, {7, 3, 3}, {7, 4, 3}, {7, 5, 3}};
+#pragma unroll
     for (int t = 0; t < 24; ++t) {
-        const int q = TET24[t][0], s = TET24[t][1], m = TET24[t][2];
+        const int q = tab[t][0], s = tab[t][1], m = tab[t][2];
         const int ox = i - (q & 1), oy = j - ((q >> 1) & 1), oz = k - ((q >> 2) & 1);
         if (ox < 0 || oy < 0 || oz < 0 || ox >= n || oy >= n || oz >= n) continue;
         int a0, a1, a2;
