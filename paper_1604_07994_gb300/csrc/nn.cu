@@ -1203,19 +1203,14 @@ int sdx_conv3(int n, int cin, int cout, const uint16_t* x, const uint16_t* w, co
               void* stream) {
     if (n < 1 || !x || !w || !y) { set_error("invalid convolution arguments"); return SDX_EINVAL; }
     API_BEGIN
-    int* err = dalloc<int>(1);
-    CK(cudaMemset(err, 0, sizeof(int)));
-    ConvArgs a{n, reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(w), bias, nullptr, relu, nullptr, y, err};
-    try {
-        launch_conv(cin, cout, a, (cudaStream_t)stream);
-    } catch (...) {
-        cudaFree(err);
-        throw;
-    }
+    DevTmp<int> err(1);
+    CK(cudaMemset(err.p, 0, sizeof(int)));
+    ConvArgs a{n, reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(w), bias, nullptr, relu, nullptr, y, err.p};
+    launch_conv(cin, cout, a, (cudaStream_t)stream);
     int e = 0;
-    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    cudaFree(err);
+    err.reset();
     if (e) { set_error("tensor-core wait timed out"); return SDX_ETIMEOUT; }
     return launched("sdx_conv3");
     API_END
@@ -1225,27 +1220,20 @@ int sdx_conv3_dgrad(int n, int cin, int cout, const uint16_t* dz, const float* w
     if (n < 1 || !dz || !w || !dx) { set_error("invalid convolution arguments"); return SDX_EINVAL; }
     API_BEGIN
     const long long nw = 27LL * cin * cout;
-    int* err = dalloc<int>(1);
-    bf16* wf = nullptr;
-    try {
-        wf = dalloc<bf16>(nw);
-        CK(cudaMemsetAsync(err, 0, sizeof(int), (cudaStream_t)stream));
-        // the network's backward path: weights flipped in the taps and transposed in the
-        // channels, then the forward kernel from the output-gradient channels to the input ones
-        count_launches(1);
-        k_flip_weights<<<eblocks(nw), ETPB, 0, (cudaStream_t)stream>>>(cin, cout, w, wf);
-        ConvArgs a{n, reinterpret_cast<const bf16*>(dz), wf, nullptr, nullptr, 0, nullptr, dx, err};
-        launch_conv(cout, cin, a, (cudaStream_t)stream);
-    } catch (...) {
-        cudaFree(err);
-        cudaFree(wf);
-        throw;
-    }
+    DevTmp<int> err(1);
+    DevTmp<bf16> wf(nw);
+    CK(cudaMemsetAsync(err.p, 0, sizeof(int), (cudaStream_t)stream));
+    // the network's backward path: weights flipped in the taps and transposed in the channels,
+    // then the forward kernel from the output-gradient channels to the input ones
+    count_launches(1);
+    k_flip_weights<<<eblocks(nw), ETPB, 0, (cudaStream_t)stream>>>(cin, cout, w, wf.p);
+    ConvArgs a{n, reinterpret_cast<const bf16*>(dz), wf.p, nullptr, nullptr, 0, nullptr, dx, err.p};
+    launch_conv(cout, cin, a, (cudaStream_t)stream);
     int e = 0;
-    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    cudaFree(err);
-    cudaFree(wf);
+    err.reset();
+    wf.reset();
     if (e) { set_error("tensor-core wait timed out"); return SDX_ETIMEOUT; }
     return launched("sdx_conv3_dgrad");
     API_END
@@ -1254,19 +1242,14 @@ int sdx_conv3_dgrad(int n, int cin, int cout, const uint16_t* dz, const float* w
 int sdx_conv3_wgrad(int n, int cin, int cout, const uint16_t* x, const uint16_t* dz, float* dw, void* stream) {
     if (n < 1 || !x || !dz || !dw) { set_error("invalid convolution arguments"); return SDX_EINVAL; }
     API_BEGIN
-    int* err = dalloc<int>(1);
-    CK(cudaMemset(err, 0, sizeof(int)));
-    try {
-        launch_wgrad(cin, cout, n, reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(dz), dw, err,
-                     (cudaStream_t)stream);
-    } catch (...) {
-        cudaFree(err);
-        throw;
-    }
+    DevTmp<int> err(1);
+    CK(cudaMemset(err.p, 0, sizeof(int)));
+    launch_wgrad(cin, cout, n, reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(dz), dw, err.p,
+                 (cudaStream_t)stream);
     int e = 0;
-    CK(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
+    CK(cudaMemcpyAsync(&e, err.p, sizeof(int), cudaMemcpyDeviceToHost, (cudaStream_t)stream));
     CK(cudaStreamSynchronize((cudaStream_t)stream));
-    cudaFree(err);
+    err.reset();
     if (e) { set_error("tensor-core wait timed out"); return SDX_ETIMEOUT; }
     return launched("sdx_conv3_wgrad");
     API_END
@@ -1278,14 +1261,14 @@ int sdx_guess_features(sdx_hier_t h, const double* f, uint16_t* x, double* fscal
     API_BEGIN
     cudaStream_t s = (cudaStream_t)stream;
     const LevelView<double> L = view<double>(*H, 0);
-    double* sc = dalloc<double>(1);
+    DevTmp<double> sc(1);
     count_launches(2);
-    k_absmax<<<1, 1024, 0, s>>>(f, 3 * L.nn, sc);
-    k_features<<<eblocks((long long)L.n * L.n * L.n), ETPB, 0, s>>>(L, f, sc, reinterpret_cast<bf16*>(x));
+    k_absmax<<<1, 1024, 0, s>>>(f, 3 * L.nn, sc.p);
+    k_features<<<eblocks((long long)L.n * L.n * L.n), ETPB, 0, s>>>(L, f, sc.p, reinterpret_cast<bf16*>(x));
     double hs = 1.0;
-    CK(cudaMemcpyAsync(&hs, sc, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(&hs, sc.p, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
-    cudaFree(sc);
+    sc.reset();
     if (fscale) *fscale = hs;
     return launched("sdx_guess_features");
     API_END
@@ -1297,13 +1280,13 @@ int sdx_guess_target(sdx_hier_t h, const double* xs, double fscale, float* t, vo
     API_BEGIN
     cudaStream_t s = (cudaStream_t)stream;
     const LevelView<double> L = view<double>(*H, 0);
-    double* pm = dalloc<double>(1);
+    DevTmp<double> pm(1);
     count_launches(2);
-    k_mean<<<1, 1024, 0, s>>>(xs + 3 * L.nn, L.nn, pm);
-    k_target<<<eblocks((long long)L.n * L.n * L.n), ETPB, 0, s>>>(L, xs, fscale, pm, t);
+    k_mean<<<1, 1024, 0, s>>>(xs + 3 * L.nn, L.nn, pm.p);
+    k_target<<<eblocks((long long)L.n * L.n * L.n), ETPB, 0, s>>>(L, xs, fscale, pm.p, t);
     const int rc = launched("sdx_guess_target");
     CK(cudaStreamSynchronize(s));
-    cudaFree(pm);
+    pm.reset();
     return rc;
     API_END
 }

@@ -583,9 +583,9 @@ static int* node_configs(const Level& L) {
         CK(cudaMemcpy(cf.data(), r->cfg, sizeof(int) * r->n, cudaMemcpyDeviceToHost));
         for (int q = 0; q < r->n; ++q) m[nd[q]] = cf[q];
     }
-    int* d = dalloc<int>(L.nn);
-    CK(cudaMemcpy(d, m.data(), sizeof(int) * L.nn, cudaMemcpyHostToDevice));
-    return d;
+    DevTmp<int> d(L.nn);
+    CK(cudaMemcpy(d.p, m.data(), sizeof(int) * L.nn, cudaMemcpyHostToDevice));
+    return d.release();
 }
 
 // The coarsest saddle matrix by probing with the device apply: columns of velocity nodes (or of
@@ -686,26 +686,18 @@ static void build_coarse(P0Handle& Q) {
     P.nf = nf;
     P.free_idx = dalloc<int>(nf);
     CK(cudaMemcpy(P.free_idx, free_idx.data(), sizeof(int) * nf, cudaMemcpyHostToDevice));
-    double* Md = dalloc<double>((long long)nb * nb);
-    double* Minv = nullptr;
-    try {
-        Minv = dalloc<double>((long long)nb * nb);
-    } catch (...) {
-        cudaFree(Md);
-        throw;
-    }
-    CK(cudaMemcpy(Md, M.data(), sizeof(double) * (size_t)nb * nb, cudaMemcpyHostToDevice));
-    const bool ok = device_inverse(Md, nb, Minv, 0);
-    cudaFree(Md);
+    DevTmp<double> Md((long long)nb * nb), Minv((long long)nb * nb);
+    CK(cudaMemcpy(Md.p, M.data(), sizeof(double) * (size_t)nb * nb, cudaMemcpyHostToDevice));
+    const bool ok = device_inverse(Md.p, nb, Minv.p, 0);
+    Md.reset();
     if (!ok) {
-        cudaFree(Minv);
         set_error("coarsest P1-P0 matrix is singular");
         throw Fail{SDX_ESINGULAR};
     }
     P.kinv = dalloc<double>((long long)nf * nf);
-    CK(cudaMemcpy2D(P.kinv, sizeof(double) * nf, Minv, sizeof(double) * nb, sizeof(double) * nf, nf,
+    CK(cudaMemcpy2D(P.kinv, sizeof(double) * nf, Minv.p, sizeof(double) * nb, sizeof(double) * nf, nf,
                     cudaMemcpyDeviceToDevice));
-    cudaFree(Minv);
+    Minv.reset();
     P.bc = dalloc<double>(nf);
     P.xc = dalloc<double>(nf);
 }

@@ -148,9 +148,9 @@ static void upload_level(Hier& H, Level& L) {
     L.info = dalloc<uint16_t>(L.nn);
     CK(cudaMemcpy(L.info, L.info_host.data(), sizeof(uint16_t) * L.nn, cudaMemcpyHostToDevice));
     auto up = [](const std::vector<int>& v) {
-        int* d = dalloc<int>((long long)v.size());
-        if (!v.empty()) CK(cudaMemcpy(d, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
-        return d;
+        DevTmp<int> d((long long)v.size());
+        if (!v.empty()) CK(cudaMemcpy(d.p, v.data(), sizeof(int) * v.size(), cudaMemcpyHostToDevice));
+        return d.release();
     };
     auto up_rows = [&](std::vector<int>* src, SpecRows& dst) {
         dst.n = (int)src[0].size();
@@ -304,20 +304,18 @@ static void build_coarse(Hier& H) {
     C.nf = nf;
     C.free_idx = dalloc<int>(nf);
     CK(cudaMemcpy(C.free_idx, free_idx.data(), sizeof(int) * nf, cudaMemcpyHostToDevice));
-    double* Md = dalloc<double>((long long)nb * nb);
-    double* Minv = dalloc<double>((long long)nb * nb);
-    CK(cudaMemcpy(Md, M.data(), sizeof(double) * (size_t)nb * nb, cudaMemcpyHostToDevice));
-    const bool ok = device_inverse(Md, nb, Minv, 0);
-    cudaFree(Md);
+    DevTmp<double> Md((long long)nb * nb), Minv((long long)nb * nb);
+    CK(cudaMemcpy(Md.p, M.data(), sizeof(double) * (size_t)nb * nb, cudaMemcpyHostToDevice));
+    const bool ok = device_inverse(Md.p, nb, Minv.p, 0);
+    Md.reset();
     if (!ok) {
-        cudaFree(Minv);
         set_error("coarsest-grid matrix is singular");
         throw Fail{SDX_ESINGULAR};
     }
     C.kinv = dalloc<double>((long long)nf * nf);
-    CK(cudaMemcpy2D(C.kinv, sizeof(double) * nf, Minv, sizeof(double) * nb, sizeof(double) * nf, nf,
+    CK(cudaMemcpy2D(C.kinv, sizeof(double) * nf, Minv.p, sizeof(double) * nb, sizeof(double) * nf, nf,
                     cudaMemcpyDeviceToDevice));
-    cudaFree(Minv);
+    Minv.reset();
     if (H.coarse_correction) {
         // Sec. 5 coarse-grid variant: the solve takes b + E b with E b = (B^T D b_p) on the free
         // velocity rows, D_a = mu_a / m_a (m_a = int lambda_a, mu_a m_a = int mu lambda_a), so

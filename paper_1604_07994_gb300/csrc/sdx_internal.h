@@ -294,6 +294,27 @@ inline T* dalloc(long long count) {
     return p;
 }
 
+// A temporary device buffer of the set-up and entry-point code, freed when it leaves scope, so
+// that a Fail thrown between its allocation and its last use does not leak it.  reset() frees it
+// early (to keep the peak footprint of the coarse-grid set-up), release() hands it to an owner.
+template <typename T>
+struct DevTmp {
+    T* p = nullptr;
+    explicit DevTmp(long long count) : p(dalloc<T>(count)) {}
+    ~DevTmp() { reset(); }
+    DevTmp(const DevTmp&) = delete;
+    DevTmp& operator=(const DevTmp&) = delete;
+    void reset() {
+        if (p) cudaFree(p);
+        p = nullptr;
+    }
+    T* release() {
+        T* q = p;
+        p = nullptr;
+        return q;
+    }
+};
+
 // SDX_OK, or SDX_ECUDA with the message set if a launch since the last check failed.
 inline int launched(const char* what) {
     cudaError_t e = cudaGetLastError();
