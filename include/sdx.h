@@ -22,7 +22,9 @@
  * the boundary conditions ("constrained") must be zero on input and are written as zero.
  * Unless stated otherwise, vector pointers are DEVICE pointers owned by the caller, and every
  * call is asynchronous on the given CUDA stream (NULL = legacy default stream); the library
- * allocates its own work buffers in sdx_create and frees them in sdx_destroy.
+ * allocates its own work buffers in sdx_create and frees them in sdx_destroy.  Calls on one
+ * handle may use its work buffers: order them on one stream (or order the streams), do not
+ * run them concurrently.
  *
  * Every function returns SDX_OK (0) or a negative error code; sdx_last_error() gives a
  * message for the calling thread's last failure.  No C++ exception crosses this interface.
@@ -400,8 +402,14 @@ int sdx_guess_refine(sdx_hier_t h, const double* b, double* x, int steps, void* 
  * plain cycles outside; direct coarsest solve (at most 12000 unknowns). */
 typedef struct sdx_p0* sdx_p0_t; /* opaque, library-owned */
 
-/* Build the hierarchy (desc->prec must be SDX_PREC_FP64; pspg_beta and coarse_correction
- * are not used) with penalty constant gamma > 0.  Synchronous.  Errors as sdx_create. */
+/* Build the hierarchy (desc->prec must be SDX_PREC_FP64; pspg_beta is not used and
+ * coarse_correction must be 0) with penalty constant gamma > 0.  Synchronous.  Errors as
+ * sdx_create, plus SDX_EINVAL for gamma <= 0 or not finite.  The handle owns every work buffer
+ * (the per-level vectors, the coarsest inverse, the Krylov basis allocated on the first
+ * FGMRES solve) until sdx_p0_destroy, which synchronises the device; NULL is a no-op.
+ * The calls below follow the conventions at the top of this file: device vectors owned by the
+ * caller, asynchronous on the stream unless stated, SDX_EINVAL for a NULL handle or vector or a
+ * level out of range, SDX_ECUDA when a launch fails. */
 int sdx_p0_create(const sdx_desc* desc, double gamma, sdx_p0_t* out);
 int sdx_p0_destroy(sdx_p0_t h);
 /* Cells per side, nodes, tetrahedra and free unknowns of one level. */
@@ -416,7 +424,8 @@ int sdx_p0_rhs(sdx_p0_t h, const double* f_nodal, double* b, void* stream);
 int sdx_p0_uzawa(sdx_p0_t h, int level, const double* b, double* x, void* stream);
 /* One V-cycle on the finest level: x += M (b - K x). */
 int sdx_p0_vcycle(sdx_p0_t h, const double* b, double* x, void* stream);
-/* Solve as sdx_solve (same arguments and return codes). */
+/* Solve as sdx_solve (same arguments and return codes; synchronises the stream, since the
+ * convergence test and FGMRES's small least-squares problem run on the host). */
 int sdx_p0_solve(sdx_p0_t h, const double* b, double* x, double rtol, int maxit, int outer, int restart,
                  sdx_stats* stats, void* stream);
 /* Local flux post-process (Sec. 3.2, remark after eq. stabc) of a finest-level vector x:
