@@ -295,7 +295,8 @@ def main():
     if rank != 0:
         return
     pk = peaks()
-    # dominant kernel: red velocity Gauss-Seidel pass of the finest level
+    # roofline objects of the finest level's red velocity and pressure passes (FP64-pipe bound);
+    # the pressure pass has the largest share of the step's launch list and is the `roofline`
     rl = extra.get("roofline_kernel", {})
     peak_fp64 = N_SM * FP64_PEAK_FLOP_PER_CLK_PER_SM * SM_MAX_MHZ * 1e6 / 1e12
     roofs = {}
