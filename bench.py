@@ -98,6 +98,23 @@ def dist_env():
     return ws, rank, local
 
 
+RESTART = 30  # FGMRES restart length of the benchmark solve
+
+
+def workload_config(n, beta, ws):
+    """The `config` object of both arms' lines: the workload and the solver, nothing measured.
+    The three-box workload has no-slip walls, so the velocities of the boundary nodes are fixed
+    and (n+1)^3 pressures + 3 (n-1)^3 interior velocities are free."""
+    free = (n + 1) ** 3 + 3 * (n - 1) ** 3
+    levels = (n // 8).bit_length()  # cells per side halve down to the 8^3 coarsest grid
+    return {"workload": f"three_boxes_{n}: {n}^3 cells ({free} free DoF), 3 seeded boxes on the 1/8 lattice, mu ratio 1e4, no-slip walls, manufactured forcing",
+            "form": "decoupled (a_tr with interface strain rows) on the finest level, a_sym on the coarser levels",
+            "solver": f"FGMRES({RESTART}) + V_var(3,3) Uzawa multigrid, {levels} levels, coarsest 8^3 dense FP64 inverse",
+            "rtol": 1e-8, "pspg_beta": beta,
+            "l2": "inputs larger than L2 (each 4-component FP64 vector is 69 MB at 128^3; solver working set > 4 GB)",
+            "parallelism": "replicas" if ws > 1 else "single GPU"}
+
+
 class ClockSampler:
     """nvidia-smi clock/throttle samples while the timed region runs."""
 
@@ -159,13 +176,14 @@ def peaks():
 
 
 # ---------------------------------------------------------------- CPU oracle leg
-def oracle_sample(seconds_budget=30.0):
+def oracle_sample(beta=1.0 / 24.0):
     """The oracle as it stands: FGMRES + V-cycle solve of the same workload family at 32^3
-    (same boxes, contrast, walls and forcing; a bounded sample of the 128^3 job)."""
+    (same boxes, contrast, walls and forcing, and the same solver: a_tr on the finest level,
+    a_sym on the coarser ones, the same beta; a bounded sample of the 128^3 job)."""
     from oracle.solvers import Hierarchy as OH, fgmres, vcycle_preconditioner
     from paper_1604_07994_gb300 import workloads as W
     p = W.three_boxes(32, 8, contrast=1e4)
-    H = OH(32, 8, p.cell_mu().ravel(), p.face, "tr")
+    H = OH(32, 8, p.cell_mu().ravel(), p.face, "tr", beta=beta, coarse_form="sym")
     L = H.levels[0]
     b = L.disc.rhs(p.nodal_forcing())
     t0 = time.perf_counter()
@@ -183,7 +201,8 @@ def oracle_sample(seconds_budget=30.0):
     return {"value": free / dt / 1e9, "unit": "GDoF/s (solved to 1e-8)", "cores": used,
             "cpu_seconds": cpu, "host_cores_available": cores, "kind": "oracle",
             "sample": f"oracle FGMRES(30)+V_var solve to 1e-8 of the same workload at 32^3 cells "
-                      f"({free} free DoF), {dt:.1f} s wall, {cpu:.1f} s CPU; scipy CSR products are "
+                      f"({free} free DoF; a_tr finest, a_sym coarser levels, beta {beta:.6g}), "
+                      f"{dt:.1f} s wall, {cpu:.1f} s CPU; scipy CSR products are "
                       f"single-threaded, the BLAS calls (dense coarsest solve, vector kernels) use the "
                       f"BLAS thread pool; cores = CPU / wall"}
 
@@ -196,7 +215,7 @@ def run_reference(args):
     times = []
     res = None
     for _ in range(args.warmup + args.steps):
-        res = oracle_sample()
+        res = oracle_sample(args.beta)
         times.append(res)
     vals = [r["value"] for r in times[args.warmup:]]
     v = float(np.mean(vals))
@@ -204,8 +223,7 @@ def run_reference(args):
             "value": v, "unit": "GDoF/s (solved to 1e-8)", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"three_boxes_{args.n}: {args.n}^3 cells, 3 seeded boxes mu ratio 1e4, no-slip, manufactured forcing, decoupled form",
-                       "solver": "FGMRES(30) + V_var(3,3) Uzawa multigrid", "rtol": 1e-8},
+            "config": workload_config(args.n, args.beta, ws),
             "cpu_baseline": {**times[-1], "value": v},
             "e2e": {"value": v, "unit": "GDoF/s (solved to 1e-8)", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -254,7 +272,6 @@ def main():
     b = torch.zeros(4 * nodes, dtype=torch.float64, device=dev)
     H.sdx_rhs(f, b)
     x = torch.zeros_like(b)
-    RESTART = 30
 
     def step(h, xv):
         xv.zero_()
@@ -323,12 +340,9 @@ def main():
         "value": value, "unit": "GDoF/s (solved to 1e-8)", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"three_boxes_{n}: {n}^3 cells ({free} free DoF), 3 seeded boxes on the 1/8 lattice, mu ratio 1e4, no-slip walls, manufactured forcing",
-                   "form": "decoupled (a_tr with interface strain rows) on the finest level, a_sym on the coarser levels",
-                   "solver": f"FGMRES({RESTART}) + V_var(3,3) Uzawa multigrid, 5 levels, coarsest 8^3 dense FP64 inverse",
-                   "rtol": 1e-8, "pspg_beta": args.beta, "time_to_1e8_s": ms * 1e-3, "iterations": iters, "final_rel_res": final_res,
-                   "setup_s": setup_s, "l2": "inputs larger than L2 (each 4-component FP64 vector is 69 MB; solver working set > 4 GB)",
-                   "parallelism": "replicas" if ws > 1 else "single GPU"},
+        "config": workload_config(n, args.beta, ws),
+        "solve": {"time_to_1e8_s": ms * 1e-3, "iterations": iters, "final_rel_res": final_res,
+                  "free_dofs": int(free), "setup_s": setup_s},
         "gpu_launches": int(launches),
         "clocks": clk,
         "roofline": roof,
@@ -444,7 +458,7 @@ def measure_details(args, H, prob, b, x, nodes, free, stream, torch, sdx, W):
         out["paper_columns"] = _guarded(lambda: run_paper(args, sdx, torch))
         out["p1p0"] = _guarded(lambda: run_p1p0(args, sdx, torch))
     if not args.no_cpu and int(os.environ.get("WORLD_SIZE", "1")) == 1:
-        out["cpu_baseline"] = _guarded(oracle_sample)
+        out["cpu_baseline"] = _guarded(lambda: oracle_sample(args.beta))
     return out
 
 
