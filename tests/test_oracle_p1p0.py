@@ -2,6 +2,8 @@
 (stabc) with gamma = 1, local flux post-process) against the paper's printed P1-P0 results and
 exact identities.  A dropped facet, a wrong weight, sign or normal, or a transposed divergence
 fails one of them."""
+import os
+
 import numpy as np
 import pytest
 import scipy.sparse as sp
@@ -13,11 +15,13 @@ from oracle.solvers import fgmres
 from oracle.transfer import prolongation
 from paper_1604_07994_gb300 import workloads as W
 
-GOLDEN = "tests/golden/relative_differences_layers_columns.txt"
-# paper Sec. 4.2.2, Table couette-results-1e3 (P1-P0, mu1/mu2 = 1e3): level, ||u - u_h||_0,
-# ||u - u_h||_V, ||p - p_h||_Q
-COUETTE = [(0, 9.5263e-03, 1.1065e-01, 6.4989e-01), (1, 2.4913e-03, 5.3663e-02, 1.3437e-01),
-           (2, 6.4259e-04, 2.6567e-02, 3.9015e-02)]
+HERE = os.path.dirname(os.path.abspath(__file__))
+GOLDEN = os.path.join(HERE, "golden", "relative_differences_layers_columns.txt")
+# Sec. 4.2.2, table couette-results-1e3 (P1-P0, mu1/mu2 = 1e3): rows (level, ||u - u_h||_0,
+# ||u - u_h||_V, ||p - p_h||_Q), read from the cited fixture
+COUETTE_GOLDEN = os.path.join(HERE, "golden", "couette_p1p0_errors_1e3.txt")
+COUETTE = [tuple(float(v) for v in line.split()) for line in open(COUETTE_GOLDEN)
+           if line.strip() and not line.startswith("#")]
 
 
 def _golden(problem, form, element):
