@@ -15,8 +15,11 @@
 // batch makes no progress for about two seconds gives up and the call returns SDX_ETIMEOUT.
 //
 // The per-node arithmetic is the code of bodies.cuh, so a V-cycle here is the same arithmetic
-// as the single-hierarchy cycle of the instance; the loads bypass L1 (LD_CG) because CTAs read
-// what other CTAs wrote earlier in the same launch, after acquiring it with a fence.
+// as the single-hierarchy cycle of the instance.  CTAs read what other CTAs wrote in earlier
+// phases of the same launch: a CTA runs a phase's first tiles only after a GPU-scope fence that
+// follows its observation of the phase's publication (the publisher fenced its writes before
+// publishing), which orders its loads after those writes, so the default variant uses plain
+// loads; a variant with L2-only loads (LD_CG) is kept for comparison.
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
