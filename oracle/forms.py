@@ -22,6 +22,9 @@ Paper passages followed here:
   (natural) - Sec. 1, eq. (boundary)
 * interface rows: test functions that are not in H^1_0 of one isoviscous subdomain, i.e. nodes
   on Gamma_12 or on a traction face - Sec. 2.2, eq. (equivalence-stencil)
+
+Test infrastructure: only tests/, the entry module's smoke check and the benchmark's CPU legs
+import it; it shares no code with the CUDA library.
 """
 from __future__ import annotations
 

@@ -8,6 +8,9 @@ refinement is again a Kuhn mesh, so the P1 spaces of consecutive levels are nest
 
 The element geometry here is computed generically (inverse of the 4x4 vertex matrix), not
 from the Kuhn shape, so that the oracle does not rely on any hand-derived stencil.
+
+Test infrastructure: only tests/, the entry module's smoke check and the benchmark's CPU legs
+import it; it shares no code with the CUDA library.
 """
 from __future__ import annotations
 

@@ -42,6 +42,9 @@ Readings of points the paper leaves open (each one is also listed in the design 
   addition of this implementation: with a floating stiff inclusion the a_tr Schur
   complement has negative directions (Sec. 3, kernel of dev sym grad) and plain Uzawa
   multigrid diverges.
+
+Test infrastructure: only tests/, the entry module's smoke check and the benchmark's CPU legs
+import it; it shares no code with the CUDA library.
 """
 from __future__ import annotations
 

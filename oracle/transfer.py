@@ -1,10 +1,13 @@
 """Nested P1 prolongation between uniformly refined Kuhn meshes.
 
-Paper Sec. 5 uses "standard restriction and prolongation operators".  For nested conforming
+Paper Sec. 5 takes the standard restriction and prolongation operators.  For nested conforming
 P1 spaces the standard prolongation is the natural embedding: a coarse P1 function is also a
 fine P1 function, so its fine nodal values are its point values.  Every fine node is either a
 coarse node or the midpoint of a coarse edge, where a linear function takes the mean of the
 two end values.  Restriction is the transpose.
+
+Test infrastructure: only tests/, the entry module's smoke check and the benchmark's CPU legs
+import it; it shares no code with the CUDA library.
 """
 from __future__ import annotations
 
