@@ -229,7 +229,9 @@ int sdx_vcycle(sdx_hier_t h, const double* b, double* x, void* stream);
  * be NULL.  Returns SDX_ENOCONV if maxit iterations did not meet rtol, SDX_ENONFINITE if a
  * residual norm was NaN/Inf (x is then the last finite iterate or garbage, stats filled),
  * SDX_ETIMEOUT if a fused smoothing launch gave up a grid barrier after its bounded wait
- * (reported at the next synchronisation; x is then not meaningful).
+ * (reported at the next synchronisation; x is then not meaningful).  With b = 0 the target
+ * is 0: from x = 0 the call returns at once (0 iterations); from any other x it iterates,
+ * driving x towards 0, until maxit (SDX_ENOCONV) - pass x = 0 for a zero right-hand side.
  * The smoothing steps of small levels may run fused in one launch when the environment sets a
  * node limit at hierarchy creation (SDX_CLUSTER_MAX_NODES / SDX_CLUSTER_MAX_NODES_FP64: one
  * thread-block cluster; SDX_COOP_MAX_NODES: a cooperative grid launch; SDX_NO_COOP=1 disables
