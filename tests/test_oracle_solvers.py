@@ -121,6 +121,42 @@ def test_discrete_solution_is_a_fixed_point_of_the_smoother(form):
     assert np.abs(y - x).max() <= 1e-9 * np.abs(x).max()
 
 
+@pytest.mark.parametrize("form", ["tr", "grad"])
+def test_colour_passes_are_exact_block_gauss_seidel_when_isoviscous(form):
+    """With one viscosity and no-slip walls there are no interface rows, so the a_tr and
+    gradient-form velocity blocks are the 7-point Laplacian per component (eq.
+    equivalence-stencil), and C is the constant-tau 7-point Laplacian: a node couples only to
+    nodes of the other colour.  One colour of the velocity pass is then an exact block solve
+    (the momentum residual vanishes on that colour's free rows, while the other colour's rows
+    still carry one), and one colour of the pressure pass scales that colour's pressure
+    residual by exactly 1 - omega.  A dropped term, a wrong colour or a wrong relaxation in a
+    pass fails this."""
+    n = 8
+    p = W.Problem(n=n, n_coarse=4, cell_id=np.zeros((n, n, n), dtype=np.uint8), mu=np.array([2.5]),
+                  face=(DIRICHLET,) * 6, forcing=W.gaussian_blobs(1))
+    L = Level(n, p.cell_mu().ravel(), p.face, form)
+    nn = L.nn
+    x = W.random_vector(n, 11).ravel()
+    x[L.con] = 0.0
+    b = W.random_vector(n, 12).ravel()
+    b[L.con] = 0.0
+    u, pr = x[: 3 * nn], x[3 * nn:]
+    f, g = b[: 3 * nn], b[3 * nn:]
+    free_v = L.free[: 3 * nn]
+    for red in (True, False):
+        col = np.tile(L.red if red else ~L.red, 3) & free_v
+        r0 = f - L.BT @ pr - L.A @ u
+        L.velocity_pass(u, pr, f, red)
+        r1 = f - L.BT @ pr - L.A @ u
+        assert np.abs(r1[col]).max() <= 1e-12 * np.abs(r0).max(), (form, red)
+        assert np.abs(r1[free_v & ~col]).max() > 1e-3 * np.abs(r0).max()  # the other colour moved
+        pc = L.red if red else ~L.red
+        s0 = (L.B @ u - g) - L.C @ pr
+        L.pressure_pass(u, pr, g, red)
+        s1 = (L.B @ u - g) - L.C @ pr
+        assert np.abs(s1[pc] - (1.0 - S.OMEGA) * s0[pc]).max() <= 1e-12 * np.abs(s0).max(), (form, red)
+
+
 @pytest.mark.parametrize("form", ["tr", "sym"])
 def test_vcycle_contracts_on_the_papers_columns_problem(form):
     """Sec. 5 runs the V_var(3,3) Uzawa multigrid on the viscosity-columns problem and
